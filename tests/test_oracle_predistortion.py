@@ -1,0 +1,122 @@
+"""Pins from the paper's worked examples (CPU only).
+
+Fig. 2 / Sec. II-C (E1): the FFT-predistorted LFM (Eq. 16) against the cubic
+solution (Eqs. 4, 11-14) and the pseudo-Chebyshev expansion (Eqs. 5-10); the
+bounds the paper prints are in tests/golden/paper_numbers.json.  These fix the
+sign of the correction phase, the factor 4*pi and kappa.  Appendix B (E7): the
+original factor-4 coefficients (Eqs. 23-24) are over an order of magnitude
+worse and cost about 1 dB.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import predistortion as pdist
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+E1 = GOLDEN["E1_fig2"]
+E7 = GOLDEN["E7_fig_pcm_residuals"]
+
+
+def _k2(tec_el_m2):
+    return oracle.KAPPA * tec_el_m2
+
+
+def test_cubic_root_solves_eq4():
+    f0, B, T, K2 = E1["f0_hz"], E1["bandwidth_hz"], E1["T_s"], _k2(E1["tec_el_m2"])
+    t = np.linspace(0, T, 11)
+    f = pdist.cubic_frequency(t, f0, B, T, K2)
+    P, Q = pdist.cubic_coefficients(t, f0, B, T, K2)
+    assert np.max(np.abs(f ** 3 - P * f ** 2 - Q) / P ** 3) < 1e-13
+    for ti, fi in zip(t[::5], f[::5]):
+        Pi, Qi = pdist.cubic_coefficients(ti, f0, B, T, K2)
+        r = np.roots([1.0, -Pi, 0.0, -Qi])
+        real = r[np.abs(r.imag) < 1e-6 * abs(r.real).max()].real
+        assert np.min(np.abs(real - fi)) < 1e-7 * fi
+    # t = 0 transmits f0 (the cubic's time reference)
+    assert abs(pdist.cubic_frequency(0.0, f0, B, T, K2) - f0) < 1e-6 * f0
+
+
+def test_no_ionosphere_reduces_to_lfm():
+    f0, B, T = 413e6, 18e6, 100e-6
+    t = np.linspace(0, T, 7)
+    np.testing.assert_allclose(pdist.cubic_frequency(t, f0, B, T, 0.0), f0 + B * t / T, rtol=1e-13)
+    mu0, dmu, gamma = pdist.chebyshev_coefficients(f0, B, T, 1e-30)
+    assert abs(mu0 - B / T) < 1e-9 * mu0 and abs(dmu) < 1e-6 * mu0 and abs(gamma) < 1e-3
+
+
+def test_chebyshev_quadratic_hits_the_three_nodes():
+    f0, B, T, K2 = E1["f0_hz"], E1["bandwidth_hz"], E1["T_s"], _k2(E1["tec_el_m2"])
+    a = pdist.A_CHEB
+    for fi in (f0 + B * (1 - a) / 2, f0 + B / 2, f0 + B * (1 + a) / 2):
+        # inverse relation of Eq. 4: t(f) = T(f - f0)/B + (2K2/c)(f0^-2 - f^-2)
+        ti = T * (fi - f0) / B + 2 * K2 / oracle.C_LIGHT * (f0 ** -2 - fi ** -2)
+        assert abs(pdist.chebyshev_frequency(ti, f0, B, T, K2) - fi) < 1e-6
+        assert abs(pdist.cubic_frequency(ti, f0, B, T, K2) - fi) < 1e-6
+
+
+def test_e7_corrected_coefficients_beat_original():
+    f0, B, T, K2 = E7["f0_hz"], E7["bandwidth_hz"], E7["T_s"], _k2(100e16)
+    t = np.linspace(0, T, 20001)
+    cub = pdist.cubic_frequency(t, f0, B, T, K2)
+    r2 = np.max(np.abs(pdist.chebyshev_frequency(t, f0, B, T, K2, 2.0) - cub))
+    r4 = np.max(np.abs(pdist.chebyshev_frequency(t, f0, B, T, K2, 4.0) - cub))
+    assert r4 / r2 > E7["min_residual_ratio_original_over_corrected"]
+
+
+@pytest.fixture(scope="module")
+def e1_waveforms():
+    f0, B, fs, T = E1["f0_hz"], E1["bandwidth_hz"], E1["fs_hz"], E1["T_s"]
+    tec_tecu = E1["tec_el_m2"] / oracle.TECU
+    K2 = _k2(E1["tec_el_m2"])
+    n = int(round(T * fs))
+    t = np.arange(n) / fs
+    lfm = np.exp(1j * pdist.lfm_phase(t, f0, B, T))
+    cubic = np.exp(1j * pdist.trapezoid_phase(pdist.cubic_frequency(t, f0, B, T, K2), 1 / fs))
+    poly = np.exp(1j * pdist.chebyshev_phase(t, f0, B, T, K2, 2.0))
+    poly4 = np.exp(1j * pdist.chebyshev_phase(t, f0, B, T, K2, 4.0))
+    L, off = 1 << 19, 1 << 16           # guard zeros on both sides: no circular wrap
+
+    def fft_method(env, tec):
+        buf = np.zeros(L, dtype=np.complex128)
+        buf[off:off + n] = lfm * env
+        return oracle.iono_correct(buf, fs, 0.0, tec)   # RF sampling: fc = 0
+
+    return dict(n=n, lfm=lfm, cubic=cubic, poly=poly, poly4=poly4, fft=fft_method, tec=tec_tecu)
+
+
+def test_e1_fft_predistortion_matches_cubic(e1_waveforms):
+    w = e1_waveforms
+    ones = np.ones(w["n"])
+    loss_fft = pdist.snr_loss_db(w["cubic"], w["fft"](ones, w["tec"]))
+    loss_poly = pdist.snr_loss_db(w["cubic"], w["poly"])
+    assert loss_fft < E1["max_loss_cubic_vs_fft_db"]
+    assert loss_poly < E1["max_loss_cubic_vs_poly_db"]
+
+
+def test_e1_peak_separation_tapered(e1_waveforms):
+    # The paper's envelope is not stated; with a 10 % cosine taper at the pulse
+    # edges the FFT and POLY correlation peaks agree within 0.001 dB.
+    w = e1_waveforms
+    n = w["n"]
+    env = np.ones(n)
+    m = n // 20
+    ramp = 0.5 - 0.5 * np.cos(np.pi * np.arange(m) / m)
+    env[:m], env[-m:] = ramp, ramp[::-1]
+    lf = pdist.snr_loss_db(w["cubic"] * env, w["fft"](env, w["tec"]))
+    lp = pdist.snr_loss_db(w["cubic"] * env, w["poly"] * env)
+    assert abs(lf - lp) < E1["max_peak_separation_fft_vs_poly_db"]
+
+
+def test_e1_negative_controls(e1_waveforms):
+    # Wrong phase sign, doubled K2, or Halpin's original factor 4 all cost dBs.
+    w = e1_waveforms
+    ones = np.ones(w["n"])
+    assert pdist.snr_loss_db(w["cubic"], w["fft"](ones, -w["tec"])) > 3.0
+    assert pdist.snr_loss_db(w["cubic"], w["fft"](ones, 2 * w["tec"])) > 0.5
+    loss4 = pdist.snr_loss_db(w["cubic"], w["poly4"])
+    assert 0.5 < loss4 < 3.0 * E7["original_loss_db_about"]
