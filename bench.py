@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark: corrected Msamples/s of the Doppler-bank workload on GB300.
+
+Workload (one step): one band-limited complex noise pulse, N = 65536 samples
+at fs = 20 MHz, fc = 1 GHz, corrected for 256 range rates U[-8, 8] km/s x 16
+TECs U[5, 150] TECU -- 32-tap Kaiser(8) windowed-sinc resampling, then FFT,
+dispersive phase multiply and inverse FFT -- through the C ABI entry point
+``correct_bank``.  One step writes 256 x 16 x 65536 = 268,435,456 corrected
+samples (2 GiB).
+
+Reported (one JSON line on rank 0):
+  value       whole-job corrected Msamples/s from per-step CUDA events on the
+              launching stream (device-resident inputs), max over ranks
+  latency_ms  p50 / p99 of the step (one bank = one pulse fully corrected)
+  plain_path  the same pulse corrected pair by pair with the single-pulse
+              entry points (doppler_resample + iono_correct), p50 / p99 per pair
+  e2e         the same metric with host buffers: pinned H2D of the pulse and
+              D2H of all corrected samples inside the timed region
+  roofline    the dominant kernel's algorithmic bytes (8 B written per
+              corrected sample) over its event-timed duration vs measured HBM
+  cpu_baseline  the FP64 oracle on a bounded sample of the same bank
+  error       max relative L2 error of the GPU result vs that oracle sample
+
+``--impl reference`` times the oracle itself (the method's plain FP64 CPU
+statement) on a bounded sample per step, on the same metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "corrected Msamples/s and p50/p99 pulse latency vs plain path at stated error"
+UNIT = "Msamples/s"
+ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
+# DRAM bytes per launch from an ncu capture of the kernel (None until taken for
+# the current kernel; summaries under profiles/).
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {}
+
+
+def load_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    if int(parts[0]) != self.index:
+                        continue
+                    rows.append(parts)
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_bank_sample(x, v, tec, cfg, n_v_sample: int):
+    """The FP64 oracle on the first n_v_sample range rates x all TECs."""
+    import oracle
+    t0 = time.perf_counter()
+    out = oracle.correct_bank(x.astype(np.complex128), cfg.fs, cfg.fc, v[:n_v_sample], tec)
+    dt = time.perf_counter() - t0
+    return out, dt
+
+
+# ------------------------------------------------------------- reference arm
+
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    cfg = synth.DopplerBank()
+    x, v, tec = cfg.draw()
+    n_v_step = 2                      # bounded sample per step: 2 v_r x 16 TEC
+    for _ in range(args.warmup):
+        oracle_bank_sample(x, v, tec, cfg, 1)
+    times = []
+    for k in range(args.steps):
+        vv = np.roll(v, -n_v_step * k)
+        _, dt = oracle_bank_sample(x, vv, tec, cfg, n_v_step)
+        times.append(dt)
+    samples = n_v_step * cfg.n_tec * cfg.n
+    value = samples * len(times) / sum(times) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(cfg),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_v_step} range rates x {cfg.n_tec} TECs x {cfg.n} samples per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+L2_NOTE = ("flushed between timed steps (256 MiB write outside the step events); "
+           "each step also writes 2 GiB")
+
+
+def workload_config(cfg) -> dict:
+    return {"workload": "doppler_bank", "n": cfg.n, "n_v": cfg.n_v, "n_tec": cfg.n_tec,
+            "fs_hz": cfg.fs, "fc_hz": cfg.fc, "taps": 32, "kaiser_beta": 8.0,
+            "signal": "unit-variance complex Gaussian low-passed to 0.8 fs/2, seeded",
+            "v_r": "U[-8, 8] km/s", "tec": "U[5, 150] TECU", "l2": L2_NOTE, "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
+    import torch
+    import paper_2508_04951_gb300 as dcg
+
+    dcg.build.build()
+    dcg.load()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    cfg = synth.DopplerBank()
+    x, v, tec = cfg.draw()
+    x32 = x.astype(np.complex64)
+    ctx = dcg.Context(local_rank)
+    stream = torch.cuda.current_stream()
+    xd = torch.from_numpy(x32).to(dev)
+    n_samples = cfg.n_v * cfg.n_tec * cfg.n
+    out = torch.empty(n_samples, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        dcg.correct_bank(ctx, xd, v, tec, out, cfg.fs, cfg.fc)
+
+    for _ in range(args.warmup):
+        step()
+    dcg.dc_check(ctx)
+
+    # ---- timed region: K steps, per-step events, L2 flushed between steps
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    dcg.dc_profile_enable(ctx, True)
+    clocks = Clocks(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = dcg.dc_launch_count(ctx)
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        events[k][0].record(stream)
+        step()
+        events[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = dcg.dc_launch_count(ctx) - launches0
+    clk = clocks.stop()
+    prof = dcg.dc_profile_read(ctx)
+    dcg.dc_profile_enable(ctx, False)
+    dcg.dc_check(ctx)
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n_samples * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- dominant kernel roofline (event-timed launches inside the timed region)
+    peak, peak_src = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][2])
+    name, (nl, ns, ms) = dom
+    achieved = ALGO_BYTES_PER_SAMPLE * ns / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": TRAFFIC_PER_LAUNCH.get(name),
+                "launch_avg_us": 1e3 * ms / nl,
+                "algorithmic_bytes_per_launch": ALGO_BYTES_PER_SAMPLE * ns / nl,
+                "phases_ms_per_step": {k: round(vv[2] / args.steps, 4) for k, vv in prof.items()}}
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(cfg),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "wall_ms_per_step": 1e3 * t_wall / args.steps,
+            "clocks": clk, "gpu_launches": int(launches), "roofline": roofline,
+        }
+
+    # ---- plain per-pulse path: each (v_r, TEC) pair alone, single-pulse entry points
+    y_tmp = torch.empty(cfg.n, dtype=torch.complex64, device=dev)
+    pairs = [(i % cfg.n_v, (7 * i) % cfg.n_tec) for i in range(args.plain_pairs + 8)]
+    pe = []
+    for j, (i, t) in enumerate(pairs):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        zslice = out[(i * cfg.n_tec + t) * cfg.n:(i * cfg.n_tec + t + 1) * cfg.n]
+        a.record(stream)
+        dcg.doppler_resample(ctx, xd, y_tmp, cfg.fs, cfg.fc, float(v[i]))
+        dcg.iono_correct(ctx, y_tmp, zslice, cfg.fs, cfg.fc, float(tec[t]))
+        b.record(stream)
+        if j >= 8:
+            pe.append((a, b))
+    torch.cuda.synchronize()
+    plain_ms = [a.elapsed_time(b) for a, b in pe]
+    if rank == 0:
+        result["plain_path"] = {
+            "value": cfg.n * len(plain_ms) / (sum(plain_ms) / 1e3) / 1e6, "unit": UNIT,
+            "p50_ms": float(np.percentile(plain_ms, 50)), "p99_ms": float(np.percentile(plain_ms, 99)),
+            "pairs_timed": len(plain_ms),
+            "what": "one (v_r, TEC) pair per call: doppler_resample + iono_correct launches"}
+
+    # ---- end to end through the C ABI with host buffers
+    k_e2e = max(1, min(args.steps, args.e2e_steps))
+    xh = torch.from_numpy(x32).pin_memory()
+    oh = torch.empty(n_samples, dtype=torch.complex64, pin_memory=True)
+    e2e_ms = []
+    for k in range(k_e2e + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        step()
+        oh.copy_(out, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    if rank == 0:
+        result["e2e"] = {"value": world * n_samples * len(e2e_ms) / (e2e_total / 1e3) / 1e6,
+                         "unit": UNIT, "h2d_bytes_per_step": int(x32.nbytes),
+                         "d2h_bytes_per_step": int(n_samples * 8), "steps": len(e2e_ms)}
+
+    # ---- CPU baseline: the oracle on a bounded sample, and the error of the
+    # GPU result on that sample (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_vs = args.cpu_sample_v
+        ref, dt = oracle_bank_sample(x, v, tec, cfg, n_vs)
+        got = oh.numpy().reshape(cfg.n_v, cfg.n_tec, cfg.n)[:n_vs].astype(np.complex128)
+        errs = np.linalg.norm(got - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+        result["cpu_baseline"] = {"value": n_vs * cfg.n_tec * cfg.n / dt / 1e6, "unit": UNIT,
+                                  "cores": 1, "kind": "oracle",
+                                  "sample": f"first {n_vs} range rates x {cfg.n_tec} TECs x {cfg.n} "
+                                            f"samples of the bank, numpy FP64 single thread, {dt:.1f} s"}
+        result["error"] = {"rel_l2_max": float(errs.max()), "rel_l2_median": float(np.median(errs)),
+                           "pairs_checked": int(errs.size), "tolerance": 1e-5}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--plain-pairs", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample-v", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

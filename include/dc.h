@@ -1,0 +1,188 @@
+/*
+ * dc.h -- C ABI of the GB300 Doppler + ionospheric correction library
+ * (libdc.so).  Method: arXiv 2508.04951, "Real-Time Doppler and Ionospheric
+ * Distortion Correction Techniques for Arbitrary Waveforms Utilizing GPU
+ * Compute".
+ *
+ * A pulse x[0..N) of complex baseband samples (interleaved float32 re/im, the
+ * layout of torch.complex64) taken at rate fs is corrected for a target range
+ * rate v_r and a total electron content TEC:
+ *
+ *   1. Doppler resampling, y[n] = x(alpha n Ts), alpha = (1 + v_r/c)/(1 - v_r/c)
+ *      (Eq. 1, Eq. 2; v_r > 0 approaching), by windowed Whittaker-Shannon
+ *      interpolation with a Kaiser-windowed sinc (Eq. 17 truncated, Sec. III-B,
+ *      Table I) or by the exact finite sum of Eq. 17.
+ *   2. Ionospheric correction (Eq. 16): y is zero-padded to L = 2^ceil(log2 n_out),
+ *      transformed, multiplied by exp(-i 4 pi K2 / (c f_k)) with K2 = kappa E
+ *      (Eq. 3), f_k = fc + fs kt/L (kt in numpy fftfreq order; fc = 0 means
+ *      the samples are RF, a bin at f_k = 0 is left unchanged), inverse
+ *      transformed with 1/L and truncated to n_out samples.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers on the context's device,
+ *    owned by the caller, 8-byte aligned (one complex sample).  Outputs must
+ *    not overlap inputs unless an entry point says so.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *    enqueued asynchronously on it; results are ready when the stream is.
+ *    Host arrays passed in (item lists, v_r/TEC lists) are read before the
+ *    call returns and may be reused afterwards.
+ *  - A context serialises its own scratch memory: do not run calls on one
+ *    context from several host threads or streams at the same time.
+ *  - Arguments are validated before anything is launched; a bad argument
+ *    returns DC_EINVAL with a message in dc_last_error() and launches
+ *    nothing.  Launch failures return DC_ECUDA.  Faults inside kernels
+ *    (bounded waits that ran out) are reported by dc_check(), which
+ *    synchronises the stream.
+ *  - Limits: 1 <= n, n_out <= 2^20 samples; |v_r| < c; fs > 0; fc == 0 or
+ *    fc > fs/2 (every bin frequency positive in baseband); even taps in
+ *    [2, 64]; Kaiser beta in [0, 20].
+ */
+#ifndef DC_H
+#define DC_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define DC_API __attribute__((visibility("default")))
+#else
+#define DC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One complex sample: interleaved float32, identical to torch.complex64. */
+typedef struct { float re, im; } dc_c64;
+
+typedef enum {
+  DC_OK = 0,
+  DC_EINVAL = 1,      /* argument rejected before any launch               */
+  DC_ENOMEM = 2,      /* device or host allocation failed                   */
+  DC_EBUSY = 3,       /* HBM budget or serve slots exhausted (try again)    */
+  DC_ECUDA = 4,       /* CUDA runtime error (launch or copy)                */
+  DC_ETIMEOUT = 5,    /* a kernel's bounded wait ran out / wait timed out   */
+  DC_ECANCELLED = 6   /* request cancelled                                  */
+} dc_status;
+
+/* Resampling method (Table I rows "Whittaker-Shannon" and "Windowed"). */
+typedef enum {
+  DC_WINDOWED = 0,        /* Kaiser-windowed sinc, `taps` taps, FP32        */
+  DC_EXACT_FP32 = 1,      /* exact finite sum of Eq. 17, FP32 CUDA cores    */
+  DC_EXACT_BF16X3 = 2,    /* exact sum as a tensor-core GEMM, bf16 hi/lo    */
+  DC_EXACT_FP16X3 = 3     /* exact sum as a tensor-core GEMM, fp16 hi/lo    */
+} dc_mode;
+
+typedef struct {
+  int taps;             /* windowed kernel length, even, default 32          */
+  double kaiser_beta;   /* Kaiser shape, default 8                           */
+  int mode;             /* dc_mode, default DC_WINDOWED                      */
+  long long n_out;      /* output samples, 0 = same as input                 */
+} dc_opts;
+
+typedef struct dc_ctx dc_ctx;
+
+/* Defaults: taps 32, beta 8, DC_WINDOWED, n_out 0. */
+DC_API void dc_opts_default(dc_opts* opts);
+
+/* Text of a status code (static storage). */
+DC_API const char* dc_status_str(int status);
+
+/* Create a context on CUDA device `device`.  It owns the twiddle tables and
+ * the scratch memory of later calls; `hbm_budget_bytes` caps that scratch
+ * (0 = no cap).  Writes the handle to *ctx.  DC_EINVAL for a bad device,
+ * DC_ENOMEM / DC_ECUDA on allocation failure. */
+DC_API dc_status dc_create(dc_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Free everything the context owns.  Synchronises the device first. */
+DC_API dc_status dc_destroy(dc_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+DC_API const char* dc_last_error(const dc_ctx* ctx);
+
+/* Synchronise `stream`, then report and clear the context's device-side
+ * error flag: DC_ETIMEOUT if a bounded wait inside a kernel ran out,
+ * DC_EINVAL if a kernel met parameters outside its range, DC_ECUDA on an
+ * asynchronous CUDA error. */
+DC_API dc_status dc_check(dc_ctx* ctx, void* stream);
+
+/* Kernels launched by this context since creation (-1 for a null context). */
+DC_API long long dc_launch_count(const dc_ctx* ctx);
+
+/* Per-phase kernel timing.  With profiling on, every kernel launch of later
+ * calls is bracketed by CUDA events recorded on the call's stream (so the
+ * times are device times of exactly that launch).  dc_profile_enable resets
+ * the totals (waiting for events still pending).  dc_profile_read waits for
+ * pending events, folds them into the totals and writes up to `max` phases
+ * (name, launches, samples covered, total ms) to `out`; returns the number
+ * of phases with at least one launch, or -1 for a null context. */
+typedef struct {
+  char name[24];
+  long long launches;
+  long long samples;
+  double ms;
+} dc_phase_time;
+DC_API dc_status dc_profile_enable(dc_ctx* ctx, int on);
+DC_API int dc_profile_read(dc_ctx* ctx, dc_phase_time* out, int max);
+
+/* Doppler resampling alone (Eq. 2 via Eq. 17; Sec. III).
+ * x_dev: [n] input samples.  y_dev: [n_out] output, n_out = opts->n_out or n.
+ * Windowed: y[j] = sum_i x[i] h(alpha j - i), h the Kaiser-windowed sinc of
+ * half width taps/2, x = 0 outside [0, n).  Exact: y[j] = sum_{i<n} x[i]
+ * sinc(alpha j - i).  fs and fc are validated only (the position alpha j is
+ * in units of samples).  opts may be NULL (defaults). */
+DC_API dc_status doppler_resample(dc_ctx* ctx, const dc_c64* x_dev, long long n, dc_c64* y_dev,
+                           double fs, double fc, double v_r, const dc_opts* opts,
+                           void* stream);
+
+/* Ionospheric correction alone (Eq. 16, Sec. II-B).  x_dev: [n] input,
+ * y_dev: [n] output; x_dev == y_dev (in place) is allowed.  tec_tecu is the
+ * TEC in units of 1e16 el/m^2; a negative TEC applies the distortion of
+ * Eq. 15 instead (the phase is linear in E). */
+DC_API dc_status iono_correct(dc_ctx* ctx, const dc_c64* x_dev, long long n, dc_c64* y_dev,
+                       double fs, double fc, double tec_tecu, void* stream);
+
+/* One pulse of a batch.  Offsets and lengths count complex samples. */
+typedef struct {
+  long long in_off;     /* first input sample in in_dev                      */
+  long long n;          /* input samples                                     */
+  long long out_off;    /* first output sample in out_dev                    */
+  long long n_out;      /* output samples (0 = n)                            */
+  double fs, fc, v_r, tec_tecu;
+} dc_item;
+
+/* Full correction of a ragged batch: for each item, resample by alpha(v_r)
+ * (opts->mode, taps, beta; opts->n_out is ignored, items carry n_out), then
+ * apply Eq. 16 with its TEC.  in_dev and out_dev hold all items at the given
+ * offsets; output ranges must not overlap each other or the inputs.  Each
+ * item's result does not depend on the other items of the batch. */
+DC_API dc_status correct_batch(dc_ctx* ctx, const dc_c64* in_dev, dc_c64* out_dev,
+                        const dc_item* items, int n_items, const dc_opts* opts,
+                        void* stream);
+
+/* Doppler bank: one pulse corrected for every (v_r, TEC) pair.
+ * x_dev: [n]; v_r: host [n_v]; tec_tecu: host [n_tec];
+ * out_dev: [n_v][n_tec][n_out] (n_out = opts->n_out or n).  Windowed mode only.
+ * Resampling and the forward transform run once per v_r, the phase multiply
+ * and inverse transform once per pair. */
+DC_API dc_status correct_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n, const double* v_r,
+                       int n_v, const double* tec_tecu, int n_tec, dc_c64* out_dev,
+                       double fs, double fc, const dc_opts* opts, void* stream);
+
+/* Exact-sinc resampling of many pulses per range rate (Eq. 17 as a dense
+ * contraction Y_a = X_a S_a^T, S_a[j][i] = sinc(alpha_a j - i)).
+ * x_dev: pulses [n_alpha][n_pulses][n] with x_alpha_stride samples between
+ *        consecutive alpha groups (0 = every alpha uses the same pulses);
+ * v_r:   host [n_alpha];
+ * y_dev: [n_alpha][n_pulses][n_out].
+ * mode:  DC_EXACT_FP32 (CUDA cores), DC_EXACT_BF16X3 or DC_EXACT_FP16X3
+ *        (tcgen05 tensor cores with hi/lo split operands, FP32 accumulation). */
+DC_API dc_status resample_exact_batch(dc_ctx* ctx, const dc_c64* x_dev, long long n, int n_pulses,
+                               long long x_alpha_stride, const double* v_r, int n_alpha,
+                               dc_c64* y_dev, long long n_out, int mode, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DC_H */

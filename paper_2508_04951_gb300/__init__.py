@@ -1,0 +1,236 @@
+"""GB300 Doppler resampling and FFT ionospheric correction (arXiv 2508.04951).
+
+Thin ctypes binding over the C ABI of ``libdc.so`` (``include/dc.h``): the
+functions here carry the C entry points' names and only marshal arguments
+(torch tensors -> device pointers, the current torch stream -> cudaStream_t,
+host lists -> C arrays).  Every step of the computation runs in the library's
+CUDA kernels; there is no CPU path.  If the library has not been built the
+import of a function that needs it raises immediately.
+
+PyTorch is used for device memory and streams only.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "DcError", "Context", "load", "lib_path",
+    "DC_WINDOWED", "DC_EXACT_FP32", "DC_EXACT_BF16X3", "DC_EXACT_FP16X3",
+    "ITEM_DTYPE", "dc_opts_default", "dc_check", "dc_launch_count", "dc_profile_enable",
+    "dc_profile_read", "doppler_resample", "iono_correct",
+    "correct_batch", "correct_bank", "resample_exact_batch", "exported_symbols",
+]
+
+DC_WINDOWED, DC_EXACT_FP32, DC_EXACT_BF16X3, DC_EXACT_FP16X3 = 0, 1, 2, 3
+STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_EBUSY", 4: "DC_ECUDA",
+          5: "DC_ETIMEOUT", 6: "DC_ECANCELLED"}
+
+# dc_item: 4 x int64 then 4 x double (64 bytes)
+ITEM_DTYPE = np.dtype([("in_off", "<i8"), ("n", "<i8"), ("out_off", "<i8"), ("n_out", "<i8"),
+                       ("fs", "<f8"), ("fc", "<f8"), ("v_r", "<f8"), ("tec_tecu", "<f8")])
+
+
+class DcOpts(ctypes.Structure):
+    _fields_ = [("taps", ctypes.c_int), ("kaiser_beta", ctypes.c_double),
+                ("mode", ctypes.c_int), ("n_out", ctypes.c_longlong)]
+
+
+class DcPhaseTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
+                ("samples", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+
+class DcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libdc.so (building it first when asked).  Raises when absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(
+                f"CUDA library {path} is not built; run paper_2508_04951_gb300.build.build() "
+                "(or __graft_entry__.build()) first")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, ll, d, i = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double, ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "dc_opts_default": (None, [ctypes.POINTER(DcOpts)]),
+        "dc_status_str": (ctypes.c_char_p, [i]),
+        "dc_create": (i, [ctypes.POINTER(vp), i, ctypes.c_size_t]),
+        "dc_destroy": (i, [vp]),
+        "dc_last_error": (ctypes.c_char_p, [vp]),
+        "dc_check": (i, [vp, vp]),
+        "dc_launch_count": (ll, [vp]),
+        "dc_profile_enable": (i, [vp, i]),
+        "dc_profile_read": (i, [vp, ctypes.POINTER(DcPhaseTime), i]),
+        "doppler_resample": (i, [vp, vp, ll, vp, d, d, d, ctypes.POINTER(DcOpts), vp]),
+        "iono_correct": (i, [vp, vp, ll, vp, d, d, d, vp]),
+        "correct_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), vp]),
+        "correct_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts), vp]),
+        "resample_exact_batch": (i, [vp, vp, ll, i, ll, dp, i, vp, ll, i, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points this binding binds (all declared in dc.h)."""
+    return ["dc_opts_default", "dc_status_str", "dc_create", "dc_destroy", "dc_last_error",
+            "dc_check", "dc_launch_count", "dc_profile_enable", "dc_profile_read", "doppler_resample", "iono_correct", "correct_batch", "correct_bank",
+            "resample_exact_batch"]
+
+
+# ---------------------------------------------------------------- helpers
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != torch.complex64:
+        raise TypeError(f"expected complex64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _opts(taps=32, beta=8.0, mode=DC_WINDOWED, n_out=0) -> DcOpts:
+    return DcOpts(int(taps), float(beta), int(mode), int(n_out))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Context:
+    """Owns a dc_ctx (twiddle tables and scratch) on one device."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.dc_create(ctypes.byref(h), int(device), int(budget_bytes))
+        if st:
+            raise DcError(st, f"dc_create(device={device}) failed")
+        self.handle = h
+
+    def check(self, st: int):
+        if st:
+            msg = self.lib.dc_last_error(self.handle).decode()
+            raise DcError(st, msg)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.dc_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dc_opts_default() -> DcOpts:
+    o = DcOpts()
+    load().dc_opts_default(ctypes.byref(o))
+    return o
+
+
+def dc_check(ctx: Context, stream=None) -> None:
+    ctx.check(ctx.lib.dc_check(ctx.handle, _stream(stream)))
+
+
+def dc_launch_count(ctx: Context) -> int:
+    return int(ctx.lib.dc_launch_count(ctx.handle))
+
+
+def dc_profile_enable(ctx: Context, on: bool = True) -> None:
+    ctx.check(ctx.lib.dc_profile_enable(ctx.handle, int(bool(on))))
+
+
+def dc_profile_read(ctx: Context) -> dict:
+    """{phase name: (launches, samples, total ms)} of the profiled calls."""
+    buf = (DcPhaseTime * 32)()
+    n = ctx.lib.dc_profile_read(ctx.handle, buf, 32)
+    if n < 0:
+        raise DcError(1, "dc_profile_read failed")
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].samples, buf[i].ms) for i in range(min(n, 32))}
+
+
+def doppler_resample(ctx: Context, x, y, fs: float, fc: float, v_r: float, *, taps=32,
+                     beta=8.0, mode=DC_WINDOWED, n_out=0, stream=None) -> None:
+    o = _opts(taps, beta, mode, n_out)
+    ctx.check(ctx.lib.doppler_resample(ctx.handle, _ptr(x), x.numel(), _ptr(y), fs, fc, v_r,
+                                       ctypes.byref(o), _stream(stream)))
+
+
+def iono_correct(ctx: Context, x, y, fs: float, fc: float, tec_tecu: float, *, stream=None) -> None:
+    ctx.check(ctx.lib.iono_correct(ctx.handle, _ptr(x), x.numel(), _ptr(y), fs, fc, tec_tecu,
+                                   _stream(stream)))
+
+
+def correct_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_WINDOWED,
+                  stream=None) -> None:
+    """items: numpy array of ITEM_DTYPE (or anything convertible to it)."""
+    it = np.ascontiguousarray(np.asarray(items, dtype=ITEM_DTYPE))
+    o = _opts(taps, beta, mode, 0)
+    ctx.check(ctx.lib.correct_batch(ctx.handle, _ptr(inp), _ptr(out), it.ctypes.data, len(it),
+                                    ctypes.byref(o), _stream(stream)))
+
+
+def correct_bank(ctx: Context, x, v_r, tec_tecu, out, fs: float, fc: float, *, taps=32,
+                 beta=8.0, n_out=0, stream=None) -> None:
+    v = np.ascontiguousarray(np.asarray(v_r, dtype=np.float64))
+    t = np.ascontiguousarray(np.asarray(tec_tecu, dtype=np.float64))
+    o = _opts(taps, beta, DC_WINDOWED, n_out)
+    ctx.check(ctx.lib.correct_bank(ctx.handle, _ptr(x), x.numel(), _dptr(v), len(v), _dptr(t),
+                                   len(t), _ptr(out), fs, fc, ctypes.byref(o), _stream(stream)))
+
+
+def resample_exact_batch(ctx: Context, x, n: int, n_pulses: int, v_r, y, *, n_out=0,
+                         x_alpha_stride=0, mode=DC_EXACT_FP32, stream=None) -> None:
+    v = np.ascontiguousarray(np.asarray(v_r, dtype=np.float64))
+    ctx.check(ctx.lib.resample_exact_batch(ctx.handle, _ptr(x), int(n), int(n_pulses),
+                                           int(x_alpha_stride), _dptr(v), len(v), _ptr(y),
+                                           int(n_out), int(mode), _stream(stream)))

@@ -1,0 +1,859 @@
+// C ABI of libdc.so (declared in include/dc.h): context, validation, host
+// parameter arithmetic in FP64 (alpha, delta, K2, phase constants) and the
+// launch sequences of each entry point.
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dc.h"
+#include "fft.cuh"
+#include "phase.cuh"
+#include "resample.cuh"
+
+using namespace dc;
+
+namespace {
+
+constexpr double kC = 299792458.0;
+// kappa = e^2 / (8 pi^2 m_e eps0), CODATA 2018 (Eq. 3)
+const double kKappa = [] {
+  const double e = 1.602176634e-19, me = 9.1093837015e-31, eps0 = 8.8541878128e-12;
+  const double pi = 3.14159265358979323846;
+  return e * e / (8.0 * pi * pi * me * eps0);
+}();
+constexpr double kPi = 3.14159265358979323846;
+constexpr long long kMaxN = 1LL << 20;
+
+}  // namespace
+
+struct dc_ctx {
+  int device = 0;
+  size_t budget = 0;
+  std::string last_error;
+  float2* tw = nullptr;       // twiddle tables (kTwSize)
+  int* err = nullptr;         // device error flag
+  char* ws = nullptr;         // scratch
+  size_t ws_bytes = 0;
+  std::vector<void*> retired; // outgrown scratch, freed at destroy
+  char* items = nullptr;      // device item arrays
+  size_t items_bytes = 0;
+  long long launches = 0;     // kernels launched by this context
+  // per-phase CUDA-event timing (dc_profile_enable / dc_profile_read)
+  bool profiling = false;
+  struct Rec { int phase; cudaEvent_t a, b; long long samples; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> pending;
+  double acc_ms[16] = {};
+  long long acc_launches[16] = {};
+  long long acc_samples[16] = {};
+  std::mutex mu;
+};
+
+namespace {
+
+dc_status fail(dc_ctx* c, dc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->last_error = buf;
+  return s;
+}
+
+dc_status cuda_fail(dc_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, DC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Kernel phases, named in dc_profile_read().
+enum Ph { PH_RS_TILED, PH_RS_DIRECT, PH_EXACT, PH_ROW_FULL, PH_COL_F1, PH_ROW_MID, PH_COL_B,
+          PH_ROW_SPEC, PH_ROW_APPLY, PH_PHASE_TABLE, PH_COUNT };
+const char* kPhaseName[PH_COUNT] = {"resample_tiled", "resample_direct", "exact_fp32", "row_full",
+                                    "col_f1", "row_mid", "col_b", "row_spec", "row_apply",
+                                    "phase_table"};
+
+cudaEvent_t take_event(dc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Counts one kernel launch; with profiling on, brackets it with events on
+// the launching stream.
+struct Phase {
+  dc_ctx* c;
+  int id;
+  cudaStream_t s;
+  long long samples;
+  cudaEvent_t a = nullptr;
+  Phase(dc_ctx* c_, int id_, cudaStream_t s_, long long samples_)
+      : c(c_), id(id_), s(s_), samples(samples_) {
+    ++c->launches;
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Phase() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, s);
+      c->pending.push_back({id, a, b, samples});
+    }
+  }
+};
+
+void split(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+int log2_ceil(long long n) {
+  int m = 0;
+  while ((1LL << m) < n) ++m;
+  return m;
+}
+
+double alpha_minus_one(double v_r) {
+  const double b = v_r / kC;
+  return (2.0 * b) / (1.0 - b);
+}
+
+// Per-pulse ionospheric constants (Eq. 16): A = 4 pi kappa E / c.
+PhaseParams phase_params(double fs, double fc, double tec_tecu, int log2L) {
+  PhaseParams p{};
+  const double A = 4.0 * kPi * kKappa * tec_tecu * 1e16 / kC;
+  split(A, p.a_hi, p.a_lo);
+  split(fc, p.fc_hi, p.fc_lo);
+  split(fs / (double)(1LL << log2L), p.d_hi, p.d_lo);
+  p.log2L = log2L;
+  p.enabled = tec_tecu != 0.0;
+  return p;
+}
+
+// Make sure the context has `bytes` of scratch (stream-ordered: the old
+// block stays allocated until destroy, since queued work may still use it).
+dc_status ensure_ws(dc_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return DC_OK;
+  if (c->budget && bytes > c->budget)
+    return fail(c, DC_EBUSY, "scratch of %zu bytes exceeds the context budget of %zu", bytes,
+                c->budget);
+  size_t want = std::max(bytes, c->ws_bytes + c->ws_bytes / 2);
+  if (c->budget) want = std::min(want, c->budget);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DC_ENOMEM, "cudaMalloc(%zu) for scratch failed: %s", want, cudaGetErrorString(e));
+  }
+  if (c->ws) c->retired.push_back(c->ws);
+  c->ws = (char*)p;
+  c->ws_bytes = want;
+  return DC_OK;
+}
+
+dc_status ensure_items(dc_ctx* c, size_t bytes) {
+  if (bytes <= c->items_bytes) return DC_OK;
+  size_t want = std::max(bytes, (size_t)1 << 16);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DC_ENOMEM, "cudaMalloc(%zu) for item lists failed", want);
+  }
+  if (c->items) c->retired.push_back(c->items);
+  c->items = (char*)p;
+  c->items_bytes = want;
+  return DC_OK;
+}
+
+// Byte layout helper for one call's scratch.
+struct Arena {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+struct KaiserTable {
+  int half, nk;
+  float inv_r2;
+  float kc[kMaxKaiser];
+};
+
+// Kaiser window as a polynomial in zeta = 1 - (u/R)^2:
+// w = I0(beta sqrt(zeta)) / I0(beta) = sum_j (beta^2/4)^j / ((j!)^2 I0(beta)) zeta^j.
+bool kaiser_table(int taps, double beta, KaiserTable& t) {
+  t.half = taps / 2;
+  t.inv_r2 = (float)(1.0 / ((double)t.half * (double)t.half));
+  double q = beta * beta / 4.0, term = 1.0, i0 = 0.0;
+  double terms[kMaxKaiser];
+  int n = 0;
+  for (int j = 0; j < kMaxKaiser; ++j) {
+    if (j > 0) term *= q / ((double)j * (double)j);
+    terms[j] = term;
+    i0 += term;
+    n = j + 1;
+    if (j > 2 && term < 1e-12 * i0) break;
+  }
+  if (n >= kMaxKaiser) return false;
+  for (int j = 0; j < n; ++j) t.kc[j] = (float)(terms[j] / i0);
+  t.nk = n;
+  return true;
+}
+
+dc_status check_opts(dc_ctx* c, const dc_opts* o) {
+  if (o->taps < 2 || o->taps > 2 * kMaxHalf || (o->taps & 1))
+    return fail(c, DC_EINVAL, "taps must be even and in [2, %d], got %d", 2 * kMaxHalf, o->taps);
+  if (!(o->kaiser_beta >= 0.0 && o->kaiser_beta <= 20.0))
+    return fail(c, DC_EINVAL, "kaiser_beta must be in [0, 20], got %g", o->kaiser_beta);
+  if (o->mode < DC_WINDOWED || o->mode > DC_EXACT_FP16X3)
+    return fail(c, DC_EINVAL, "unknown mode %d", o->mode);
+  if (o->n_out < 0 || o->n_out > kMaxN)
+    return fail(c, DC_EINVAL, "n_out must be in [0, 2^20], got %lld", o->n_out);
+  return DC_OK;
+}
+
+dc_status check_pulse(dc_ctx* c, long long n, long long n_out, double fs, double fc, double v_r,
+                      double tec) {
+  if (n < 1 || n > kMaxN) return fail(c, DC_EINVAL, "n must be in [1, 2^20], got %lld", n);
+  if (n_out < 1 || n_out > kMaxN)
+    return fail(c, DC_EINVAL, "n_out must be in [1, 2^20], got %lld", n_out);
+  if (!(fs > 0.0) || !std::isfinite(fs)) return fail(c, DC_EINVAL, "fs must be > 0, got %g", fs);
+  if (!(fc >= 0.0) || !std::isfinite(fc)) return fail(c, DC_EINVAL, "fc must be >= 0, got %g", fc);
+  if (fc != 0.0 && !(fc > fs / 2.0))
+    return fail(c, DC_EINVAL, "baseband needs fc > fs/2 (fc=%g, fs=%g); fc = 0 means RF samples", fc,
+                fs);
+  if (!(std::fabs(v_r) < kC)) return fail(c, DC_EINVAL, "|v_r| must be < c, got %g", v_r);
+  if (!std::isfinite(tec)) return fail(c, DC_EINVAL, "tec must be finite");
+  return DC_OK;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Upload an item array to the context's device item buffer (stream-ordered;
+// the pageable source may be reused as soon as this returns).
+template <class T>
+dc_status upload(dc_ctx* c, const std::vector<T>& v, size_t at, cudaStream_t s, const T** dev) {
+  cudaError_t e = cudaMemcpyAsync(c->items + at, v.data(), v.size() * sizeof(T),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "item upload");
+  *dev = reinterpret_cast<const T*>(c->items + at);
+  return DC_OK;
+}
+
+// ------------------------------------------------------------ resampling
+// Windowed resample of `items` (host list, tile_begin filled here).
+dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, size_t item_at,
+                       cudaStream_t s) {
+  if (items.empty()) return DC_OK;
+  KaiserTable kt;
+  if (!kaiser_table(o.taps, o.kaiser_beta, kt)) return fail(c, DC_EINVAL, "kaiser table overflow");
+  // Split into the tiled launch (32 taps, |delta| <= 0.01) and the direct one.
+  std::vector<RsItem> tiled, direct;
+  for (auto& it : items) {
+    const double dl = (double)it.dl_hi + (double)it.dl_lo;
+    (o.taps == 32 && std::fabs(dl) <= kRsTiledMaxDelta ? tiled : direct).push_back(it);
+  }
+  size_t at = item_at;
+  for (int pass = 0; pass < 2; ++pass) {
+    auto& v = pass == 0 ? tiled : direct;
+    if (v.empty()) continue;
+    int tiles = 0;
+    for (auto& it : v) {
+      it.tile_begin = tiles;
+      tiles += (int)((it.n_out + kRsTile - 1) / kRsTile);
+    }
+    const RsItem* dev = nullptr;
+    dc_status st = upload(c, v, at, s, &dev);
+    if (st) return st;
+    at += (v.size() * sizeof(RsItem) + 255) & ~(size_t)255;
+    RsArgs a{};
+    a.items = dev;
+    a.n_items = (int)v.size();
+    a.n_tiles = tiles;
+    a.half = kt.half;
+    a.nk = kt.nk;
+    a.inv_r2 = kt.inv_r2;
+    memcpy(a.kc, kt.kc, sizeof(float) * kt.nk);
+    a.err = c->err;
+    long long outs = 0;
+    for (auto& it : v) outs += it.n_out;
+    Phase ph(c, pass == 0 ? PH_RS_TILED : PH_RS_DIRECT, s, outs);
+    cudaError_t e = pass == 0 ? launch_resample_tiled32(a, s) : launch_resample_direct(a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resample launch");
+  }
+  return DC_OK;
+}
+
+size_t items_bytes_for(size_t n) { return ((n * 128 + 255) & ~(size_t)255) + 4096; }
+
+// ------------------------------------------------------ correction pipeline
+// One L class of pulses already resampled into y; writes corrected outputs.
+// Four-step classes use T (L samples per item) from the scratch.
+dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2* T,
+                         size_t& item_at, cudaStream_t s) {
+  if (it.empty()) return DC_OK;
+  const FftItem* dev = nullptr;
+  cudaError_t e;
+  if (log2L <= 12) {
+    dc_status st = upload(c, it, item_at, s, &dev);
+    if (st) return st;
+    item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
+    RowArgs a{dev, (int)it.size(), log2L, 0, c->tw};
+    long long outs = 0;
+    for (auto& f : it) outs += f.n_out;
+    Phase ph(c, PH_ROW_FULL, s, outs);
+    e = launch_row(ROW_FULL, a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "row launch");
+    return DC_OK;
+  }
+  const int log2L1 = log2L - 12;
+  const size_t L = (size_t)1 << log2L;
+  // pass 1: y -> T ; pass 2: T in place ; pass 3: T -> out
+  std::vector<FftItem> p1 = it, p2 = it, p3 = it;
+  for (size_t i = 0; i < it.size(); ++i) {
+    float2* Ti = T + i * L;
+    p1[i].dst = Ti;
+    p2[i].src = Ti;
+    p2[i].dst = Ti;
+    p3[i].src = Ti;
+  }
+  const FftItem *d1, *d2, *d3;
+  dc_status st;
+  if ((st = upload(c, p1, item_at, s, &d1))) return st;
+  item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
+  if ((st = upload(c, p2, item_at, s, &d2))) return st;
+  item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
+  if ((st = upload(c, p3, item_at, s, &d3))) return st;
+  item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
+  long long outs = 0;
+  for (auto& f : it) outs += f.n_out;
+  ColArgs a1{d1, (int)it.size(), log2L, log2L1, c->tw};
+  {
+    Phase ph(c, PH_COL_F1, s, outs);
+    if ((e = launch_col(COL_F1, a1, s)) != cudaSuccess) return cuda_fail(c, e, "col F1 launch");
+  }
+  RowArgs a2{d2, (int)it.size(), log2L, log2L1, c->tw};
+  {
+    Phase ph(c, PH_ROW_MID, s, outs);
+    if ((e = launch_row(ROW_MID, a2, s)) != cudaSuccess) return cuda_fail(c, e, "row launch");
+  }
+  ColArgs a3{d3, (int)it.size(), log2L, log2L1, c->tw};
+  {
+    Phase ph(c, PH_COL_B, s, outs);
+    if ((e = launch_col(COL_B, a3, s)) != cudaSuccess) return cuda_fail(c, e, "col B launch");
+  }
+  return DC_OK;
+}
+
+}  // namespace
+
+// ==================================================================== ABI
+extern "C" {
+
+void dc_opts_default(dc_opts* o) {
+  if (!o) return;
+  o->taps = 32;
+  o->kaiser_beta = 8.0;
+  o->mode = DC_WINDOWED;
+  o->n_out = 0;
+}
+
+const char* dc_status_str(int s) {
+  switch (s) {
+    case DC_OK: return "DC_OK";
+    case DC_EINVAL: return "DC_EINVAL";
+    case DC_ENOMEM: return "DC_ENOMEM";
+    case DC_EBUSY: return "DC_EBUSY";
+    case DC_ECUDA: return "DC_ECUDA";
+    case DC_ETIMEOUT: return "DC_ETIMEOUT";
+    case DC_ECANCELLED: return "DC_ECANCELLED";
+    default: return "DC_UNKNOWN";
+  }
+}
+
+dc_status dc_create(dc_ctx** out, int device, size_t budget) {
+  if (!out) return DC_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DC_ECUDA;
+  }
+  if (device < 0 || device >= count) return DC_EINVAL;
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return DC_ECUDA;
+  dc_ctx* c = new (std::nothrow) dc_ctx();
+  if (!c) return DC_ENOMEM;
+  c->device = device;
+  c->budget = budget;
+  // Twiddle tables in FP64, rounded to float (layout in common.cuh).
+  std::vector<float2> tw(kTwSize);
+  for (int t = 0; t < 4096; ++t) {
+    const double a = -2.0 * kPi * t / 4096.0;
+    tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  for (int j = 0; j < 1024; ++j) {
+    const double a = -2.0 * kPi * j / (double)(1 << 20);
+    tw[kTwLo + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    const double b = -2.0 * kPi * j / 1024.0;
+    tw[kTwHi + j] = make_float2((float)std::cos(b), (float)std::sin(b));
+  }
+  if ((e = cudaMalloc(&c->tw, sizeof(float2) * kTwSize)) != cudaSuccess ||
+      (e = cudaMemcpy(c->tw, tw.data(), sizeof(float2) * kTwSize, cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMalloc(&c->err, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(c->err, 0, sizeof(int))) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->tw) cudaFree(c->tw);
+    if (c->err) cudaFree(c->err);
+    delete c;
+    return DC_ENOMEM;
+  }
+  *out = c;
+  return DC_OK;
+}
+
+dc_status dc_destroy(dc_ctx* c) {
+  if (!c) return DC_EINVAL;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (auto& r : c->pending) c->pool.push_back(r.a), c->pool.push_back(r.b);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  for (void* p : c->retired) cudaFree(p);
+  if (c->ws) cudaFree(c->ws);
+  if (c->items) cudaFree(c->items);
+  if (c->tw) cudaFree(c->tw);
+  if (c->err) cudaFree(c->err);
+  delete c;
+  return DC_OK;
+}
+
+const char* dc_last_error(const dc_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+long long dc_launch_count(const dc_ctx* c) { return c ? c->launches : -1; }
+
+dc_status dc_profile_enable(dc_ctx* c, int on) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  for (auto& r : c->pending) {
+    cudaEventSynchronize(r.b);
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->pending.clear();
+  for (int i = 0; i < 16; ++i) c->acc_ms[i] = 0, c->acc_launches[i] = 0, c->acc_samples[i] = 0;
+  c->profiling = on != 0;
+  return DC_OK;
+}
+
+int dc_profile_read(dc_ctx* c, dc_phase_time* out, int max) {
+  if (!c) return -1;
+  std::lock_guard<std::mutex> g(c->mu);
+  for (auto& r : c->pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    c->acc_ms[r.phase] += ms;
+    c->acc_launches[r.phase] += 1;
+    c->acc_samples[r.phase] += r.samples;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->pending.clear();
+  int n = 0;
+  for (int i = 0; i < PH_COUNT; ++i) {
+    if (!c->acc_launches[i]) continue;
+    if (out && n < max) {
+      memset(out[n].name, 0, sizeof out[n].name);
+      strncpy(out[n].name, kPhaseName[i], sizeof out[n].name - 1);
+      out[n].launches = c->acc_launches[i];
+      out[n].samples = c->acc_samples[i];
+      out[n].ms = c->acc_ms[i];
+    }
+    ++n;
+  }
+  return n;
+}
+
+dc_status dc_check(dc_ctx* c, void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaError_t e = cudaStreamSynchronize(S(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  int flag = 0;
+  if ((e = cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "error flag read");
+  if (flag) {
+    cudaMemset(c->err, 0, sizeof(int));
+    if (flag == 1) return fail(c, DC_ETIMEOUT, "a kernel's bounded wait ran out");
+    return fail(c, DC_EINVAL, "a kernel met parameters outside its range (code %d)", flag);
+  }
+  return DC_OK;
+}
+
+dc_status doppler_resample(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, double fs,
+                           double fc, double v_r, const dc_opts* opts, void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  dc_status st = check_opts(c, &o);
+  if (st) return st;
+  const long long n_out = o.n_out ? o.n_out : n;
+  if ((st = check_pulse(c, n, n_out, fs, fc, v_r, 0.0))) return st;
+  if (!x || !y) return fail(c, DC_EINVAL, "null buffer");
+  cudaSetDevice(c->device);
+  const double dl = alpha_minus_one(v_r);
+  cudaStream_t s = S(stream);
+  if ((st = ensure_items(c, items_bytes_for(4)))) return st;
+  if (o.mode == DC_WINDOWED) {
+    std::vector<RsItem> items(1);
+    items[0].x = reinterpret_cast<const float2*>(x);
+    items[0].y = reinterpret_cast<float2*>(y);
+    items[0].n_in = (int)n;
+    items[0].n_out = (int)n_out;
+    split(dl, items[0].dl_hi, items[0].dl_lo);
+    return run_windowed(c, items, o, 0, s);
+  }
+  if (o.mode != DC_EXACT_FP32) return fail(c, DC_EINVAL, "single-pulse exact resampling uses FP32");
+  std::vector<ExItem> ex(1);
+  ex[0].x = reinterpret_cast<const float2*>(x);
+  ex[0].y = reinterpret_cast<float2*>(y);
+  split(dl, ex[0].dl_hi, ex[0].dl_lo);
+  const ExItem* dev = nullptr;
+  if ((st = upload(c, ex, 0, s, &dev))) return st;
+  ExArgs a{dev, (int)n, (int)n_out, 1};
+  Phase ph(c, PH_EXACT, s, n_out);
+  cudaError_t e = launch_exact_fp32(a, 1, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exact launch");
+  return DC_OK;
+}
+
+dc_status iono_correct(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, double fs, double fc,
+                       double tec, void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  dc_status st = check_pulse(c, n, n, fs, fc, 0.0, tec);
+  if (st) return st;
+  if (!x || !y) return fail(c, DC_EINVAL, "null buffer");
+  cudaSetDevice(c->device);
+  const int log2L = log2_ceil(n);
+  const size_t L = (size_t)1 << log2L;
+  if ((st = ensure_ws(c, log2L > 12 ? L * sizeof(float2) : 256))) return st;
+  if ((st = ensure_items(c, items_bytes_for(8)))) return st;
+  std::vector<FftItem> it(1);
+  it[0].src = reinterpret_cast<const float2*>(x);
+  it[0].dst = reinterpret_cast<float2*>(y);
+  it[0].ptab = nullptr;
+  it[0].ph = phase_params(fs, fc, tec, log2L);
+  it[0].n_valid = (int)n;
+  it[0].n_out = (int)n;
+  size_t at = 0;
+  return run_iono_class(c, it, log2L, reinterpret_cast<float2*>(c->ws), at, S(stream));
+}
+
+dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item* items,
+                        int n_items, const dc_opts* opts, void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  dc_status st = check_opts(c, &o);
+  if (st) return st;
+  if (n_items < 0 || (n_items > 0 && (!items || !in || !out)))
+    return fail(c, DC_EINVAL, "bad item list");
+  if (n_items == 0) return DC_OK;
+  if (o.mode != DC_WINDOWED && o.mode != DC_EXACT_FP32)
+    return fail(c, DC_EINVAL, "correct_batch supports DC_WINDOWED and DC_EXACT_FP32");
+  for (int i = 0; i < n_items; ++i) {
+    const dc_item& it = items[i];
+    const long long no = it.n_out ? it.n_out : it.n;
+    if ((st = check_pulse(c, it.n, no, it.fs, it.fc, it.v_r, it.tec_tecu)))
+      return fail(c, st, "item %d: %s", i, c->last_error.c_str());
+    if (it.in_off < 0 || it.out_off < 0) return fail(c, DC_EINVAL, "item %d: negative offset", i);
+  }
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
+  const float2* X = reinterpret_cast<const float2*>(in);
+  float2* Y = reinterpret_cast<float2*>(out);
+
+  // Scratch: resampled y per item, then four-step T per item of L > 4096.
+  Arena ar;
+  std::vector<size_t> yoff(n_items), toff(n_items, 0);
+  std::vector<int> log2L(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    const long long no = items[i].n_out ? items[i].n_out : items[i].n;
+    yoff[i] = ar.take((size_t)no * sizeof(float2));
+    log2L[i] = log2_ceil(no);
+  }
+  // Group by L.
+  std::vector<std::vector<int>> by_L(21);
+  for (int i = 0; i < n_items; ++i) by_L[log2L[i]].push_back(i);
+  std::vector<size_t> class_T(21, 0);
+  for (int m = 13; m <= 20; ++m)
+    if (!by_L[m].empty()) class_T[m] = ar.take(by_L[m].size() * ((size_t)1 << m) * sizeof(float2));
+  if ((st = ensure_ws(c, ar.off))) return st;
+  if ((st = ensure_items(c, items_bytes_for((size_t)n_items * 4)))) return st;
+  char* ws = c->ws;
+  size_t item_at = 0;
+
+  // 1. resampling
+  if (o.mode == DC_WINDOWED) {
+    std::vector<RsItem> rs(n_items);
+    for (int i = 0; i < n_items; ++i) {
+      const dc_item& it = items[i];
+      rs[i].x = X + it.in_off;
+      rs[i].y = reinterpret_cast<float2*>(ws + yoff[i]);
+      rs[i].n_in = (int)it.n;
+      rs[i].n_out = (int)(it.n_out ? it.n_out : it.n);
+      split(alpha_minus_one(it.v_r), rs[i].dl_hi, rs[i].dl_lo);
+    }
+    if ((st = run_windowed(c, rs, o, item_at, s))) return st;
+    item_at += 2 * ((n_items * sizeof(RsItem) + 255) & ~(size_t)255);
+  } else {
+    for (int i = 0; i < n_items; ++i) {
+      const dc_item& it = items[i];
+      std::vector<ExItem> ex(1);
+      ex[0].x = X + it.in_off;
+      ex[0].y = reinterpret_cast<float2*>(ws + yoff[i]);
+      split(alpha_minus_one(it.v_r), ex[0].dl_hi, ex[0].dl_lo);
+      const ExItem* dev = nullptr;
+      if ((st = upload(c, ex, item_at, s, &dev))) return st;
+      item_at += 256;
+      ExArgs a{dev, (int)it.n, (int)(it.n_out ? it.n_out : it.n), 1};
+      Phase ph(c, PH_EXACT, s, a.n_out);
+      cudaError_t e = launch_exact_fp32(a, 1, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "exact launch");
+    }
+  }
+  // 2. ionospheric correction per L class
+  for (int m = 0; m <= 20; ++m) {
+    if (by_L[m].empty()) continue;
+    std::vector<FftItem> fi(by_L[m].size());
+    for (size_t j = 0; j < by_L[m].size(); ++j) {
+      const int i = by_L[m][j];
+      const dc_item& it = items[i];
+      const int no = (int)(it.n_out ? it.n_out : it.n);
+      fi[j].src = reinterpret_cast<const float2*>(ws + yoff[i]);
+      fi[j].dst = Y + it.out_off;
+      fi[j].ptab = nullptr;
+      fi[j].ph = phase_params(it.fs, it.fc, it.tec_tecu, m);
+      fi[j].n_valid = no;
+      fi[j].n_out = no;
+    }
+    float2* T = reinterpret_cast<float2*>(ws + class_T[m]);
+    if ((st = run_iono_class(c, fi, m, T, item_at, s))) return st;
+  }
+  return DC_OK;
+}
+
+}  // extern "C"
+
+// Phase table for the bank: P[t][k] = exp(-i phi_k(TEC_t)).
+namespace dc {
+__global__ void phase_table_kernel(const PhaseParams* ph, int n_tec, int log2L, float2* P) {
+  const size_t L = (size_t)1 << log2L;
+  const size_t total = L * (size_t)n_tec;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(g >> log2L), k = (int)(g & (L - 1));
+    P[g] = ph[t].enabled ? iono_factor(ph[t], k) : make_float2(1.f, 0.f);
+  }
+}
+}  // namespace dc
+
+extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const double* v_r,
+                                  int n_v, const double* tec, int n_tec, dc_c64* out, double fs,
+                                  double fc, const dc_opts* opts, void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  dc_status st = check_opts(c, &o);
+  if (st) return st;
+  if (o.mode != DC_WINDOWED) return fail(c, DC_EINVAL, "correct_bank supports DC_WINDOWED");
+  if (n_v < 1 || n_tec < 1 || !v_r || !tec || !x || !out)
+    return fail(c, DC_EINVAL, "bad bank lists");
+  const long long n_out = o.n_out ? o.n_out : n;
+  for (int i = 0; i < n_v; ++i)
+    if ((st = check_pulse(c, n, n_out, fs, fc, v_r[i], 0.0))) return st;
+  for (int t = 0; t < n_tec; ++t)
+    if (!std::isfinite(tec[t])) return fail(c, DC_EINVAL, "tec[%d] not finite", t);
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
+  const int log2L = log2_ceil(n_out);
+  const size_t L = (size_t)1 << log2L;
+  const bool four = log2L > 12;
+  // Transforms per chunk of the inverse (four-step T kept small enough to
+  // stay in L2 between its two passes).
+  const int chunk = four ? std::max(1, (int)((64ull << 20) / (L * sizeof(float2)))) : n_v * n_tec;
+  Arena ar;
+  const size_t y_at = ar.take((size_t)n_v * n_out * sizeof(float2));
+  const size_t p_at = ar.take((size_t)n_tec * L * sizeof(float2));
+  const size_t s_at = ar.take((size_t)n_v * L * sizeof(float2));
+  const size_t t_at = ar.take((size_t)std::max(chunk, four ? n_v : 0) * L * sizeof(float2));
+  const size_t ph_at = ar.take((size_t)n_tec * sizeof(PhaseParams));
+  if ((st = ensure_ws(c, ar.off))) return st;
+  const size_t n_pairs = (size_t)n_v * n_tec;
+  if ((st = ensure_items(c, items_bytes_for(n_pairs * 2 + n_v * 6)))) return st;
+  char* ws = c->ws;
+  float2* Yr = reinterpret_cast<float2*>(ws + y_at);
+  float2* P = reinterpret_cast<float2*>(ws + p_at);
+  float2* Sp = reinterpret_cast<float2*>(ws + s_at);
+  float2* T = reinterpret_cast<float2*>(ws + t_at);
+  size_t item_at = 0;
+  cudaError_t e;
+
+  // 1. phase table
+  std::vector<PhaseParams> ph(n_tec);
+  for (int t = 0; t < n_tec; ++t) ph[t] = phase_params(fs, fc, tec[t], log2L);
+  if ((e = cudaMemcpyAsync(ws + ph_at, ph.data(), n_tec * sizeof(PhaseParams),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "phase upload");
+  {
+    const size_t total = L * n_tec;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    Phase ph(c, PH_PHASE_TABLE, s, (long long)total);
+    phase_table_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const PhaseParams*>(ws + ph_at), n_tec,
+                                             log2L, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "phase table launch");
+  }
+  // 2. resample per v_r
+  std::vector<RsItem> rs(n_v);
+  for (int i = 0; i < n_v; ++i) {
+    rs[i].x = reinterpret_cast<const float2*>(x);
+    rs[i].y = Yr + (size_t)i * n_out;
+    rs[i].n_in = (int)n;
+    rs[i].n_out = (int)n_out;
+    split(alpha_minus_one(v_r[i]), rs[i].dl_hi, rs[i].dl_lo);
+  }
+  if ((st = run_windowed(c, rs, o, item_at, s))) return st;
+  item_at += 2 * ((n_v * sizeof(RsItem) + 255) & ~(size_t)255);
+  // 3. spectra per v_r
+  std::vector<FftItem> sp(n_v);
+  for (int i = 0; i < n_v; ++i) {
+    sp[i] = FftItem{};
+    sp[i].src = Yr + (size_t)i * n_out;
+    sp[i].dst = Sp + (size_t)i * L;
+    sp[i].n_valid = (int)n_out;
+    sp[i].n_out = (int)n_out;
+  }
+  const FftItem* dev = nullptr;
+  if (!four) {
+    if ((st = upload(c, sp, item_at, s, &dev))) return st;
+    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
+    RowArgs a{dev, n_v, log2L, 0, c->tw};
+    Phase ph(c, PH_ROW_SPEC, s, (long long)n_v * n_out);
+    if ((e = launch_row(ROW_SPEC, a, s)) != cudaSuccess) return cuda_fail(c, e, "spec launch");
+  } else {
+    std::vector<FftItem> f1 = sp, f2 = sp;
+    for (int i = 0; i < n_v; ++i) {
+      f1[i].dst = T + (size_t)i * L;
+      f2[i].src = T + (size_t)i * L;
+    }
+    if ((st = upload(c, f1, item_at, s, &dev))) return st;
+    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
+    ColArgs a1{dev, n_v, log2L, log2L - 12, c->tw};
+    {
+      Phase ph(c, PH_COL_F1, s, (long long)n_v * n_out);
+      if ((e = launch_col(COL_F1, a1, s)) != cudaSuccess) return cuda_fail(c, e, "F1 launch");
+    }
+    if ((st = upload(c, f2, item_at, s, &dev))) return st;
+    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
+    RowArgs a2{dev, n_v, log2L, log2L - 12, c->tw};
+    Phase ph(c, PH_ROW_SPEC, s, (long long)n_v * n_out);
+    if ((e = launch_row(ROW_SPEC, a2, s)) != cudaSuccess) return cuda_fail(c, e, "F2 launch");
+  }
+  // 4. phase + inverse per (v_r, TEC), in chunks
+  std::vector<FftItem> ap(n_pairs);
+  for (int i = 0; i < n_v; ++i)
+    for (int t = 0; t < n_tec; ++t) {
+      FftItem& f = ap[(size_t)i * n_tec + t];
+      f = FftItem{};
+      f.src = Sp + (size_t)i * L;
+      f.ptab = P + (size_t)t * L;
+      f.dst = reinterpret_cast<float2*>(out) + ((size_t)i * n_tec + t) * n_out;
+      f.n_valid = (int)n_out;
+      f.n_out = (int)n_out;
+    }
+  if (!four) {
+    if ((st = upload(c, ap, item_at, s, &dev))) return st;
+    RowArgs a{dev, (int)n_pairs, log2L, 0, c->tw};
+    Phase ph(c, PH_ROW_APPLY, s, (long long)n_pairs * n_out);
+    if ((e = launch_row(ROW_APPLY, a, s)) != cudaSuccess) return cuda_fail(c, e, "apply launch");
+    return DC_OK;
+  }
+  std::vector<FftItem> ra = ap, cb = ap;
+  for (size_t j = 0; j < n_pairs; ++j) {
+    float2* Tj = T + (j % (size_t)chunk) * L;
+    ra[j].dst = Tj;
+    cb[j].src = Tj;
+  }
+  const FftItem *dra = nullptr, *dcb = nullptr;
+  if ((st = upload(c, ra, item_at, s, &dra))) return st;
+  item_at += (n_pairs * sizeof(FftItem) + 255) & ~(size_t)255;
+  if ((st = upload(c, cb, item_at, s, &dcb))) return st;
+  for (size_t j0 = 0; j0 < n_pairs; j0 += chunk) {
+    const int cnt = (int)std::min<size_t>(chunk, n_pairs - j0);
+    RowArgs a{dra + j0, cnt, log2L, log2L - 12, c->tw};
+    {
+      Phase ph(c, PH_ROW_APPLY, s, (long long)cnt * n_out);
+      if ((e = launch_row(ROW_APPLY, a, s)) != cudaSuccess) return cuda_fail(c, e, "apply launch");
+    }
+    ColArgs b{dcb + j0, cnt, log2L, log2L - 12, c->tw};
+    {
+      Phase ph(c, PH_COL_B, s, (long long)cnt * n_out);
+      if ((e = launch_col(COL_B, b, s)) != cudaSuccess) return cuda_fail(c, e, "B launch");
+    }
+  }
+  return DC_OK;
+}
+
+extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long n, int n_pulses,
+                                          long long stride, const double* v_r, int n_alpha,
+                                          dc_c64* y, long long n_out, int mode, void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (!x || !y || !v_r || n_alpha < 1 || n_pulses < 1)
+    return fail(c, DC_EINVAL, "bad exact-batch arguments");
+  if (n_out == 0) n_out = n;
+  dc_status st;
+  for (int i = 0; i < n_alpha; ++i)
+    if ((st = check_pulse(c, n, n_out, 1.0, 0.0, v_r[i], 0.0))) return st;
+  if (stride < 0) return fail(c, DC_EINVAL, "negative alpha stride");
+  if (mode != DC_EXACT_FP32)
+    return fail(c, DC_EINVAL, "mode %d not available in this build", mode);
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
+  if ((st = ensure_items(c, items_bytes_for(n_alpha)))) return st;
+  std::vector<ExItem> ex(n_alpha);
+  for (int i = 0; i < n_alpha; ++i) {
+    ex[i].x = reinterpret_cast<const float2*>(x) + (size_t)i * stride;
+    ex[i].y = reinterpret_cast<float2*>(y) + (size_t)i * n_pulses * n_out;
+    split(alpha_minus_one(v_r[i]), ex[i].dl_hi, ex[i].dl_lo);
+  }
+  const ExItem* dev = nullptr;
+  if ((st = upload(c, ex, 0, s, &dev))) return st;
+  ExArgs a{dev, (int)n, (int)n_out, n_pulses};
+  Phase ph(c, PH_EXACT, s, (long long)n_alpha * n_pulses * n_out);
+  cudaError_t e = launch_exact_fp32(a, n_alpha, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exact launch");
+  return DC_OK;
+}

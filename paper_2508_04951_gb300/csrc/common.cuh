@@ -1,0 +1,189 @@
+// Device-side building blocks shared by the library's kernels: complex
+// arithmetic on float2, error-free float transforms (double-float), the
+// in-register DFTs of radix 2/4/8/16 used by the Stockham stages, and the
+// twiddle tables' layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DC_DEV __device__ __forceinline__
+
+namespace dc {
+
+// ---------------------------------------------------------------- complex
+DC_DEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+DC_DEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+DC_DEV float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+DC_DEV float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (DIR < 0) or +i (DIR > 0)
+template <int DIR> DC_DEV float2 mul_i(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+template <int DIR> DC_DEV float2 conj_if(float2 w) {
+  return DIR < 0 ? w : make_float2(w.x, -w.y);
+}
+
+// ------------------------------------------------------------ double-float
+// Dekker/Knuth error-free transforms: a value is hi + lo with |lo| <= ulp(hi)/2.
+struct df { float hi, lo; };
+DC_DEV df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+DC_DEV df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+DC_DEV df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return two_sum(s.hi, lo);
+}
+// (a.hi + a.lo) * k for a float k
+DC_DEV df df_mul_f(df a, float k) {
+  df p = two_prod(a.hi, k);
+  return two_sum(p.hi, fmaf(a.lo, k, p.lo));
+}
+// a / b, both double-float
+DC_DEV df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df p = two_prod(q1, b.hi);
+  float r = __fsub_rn(a.hi, p.hi);          // exact: q1*b.hi is within an ulp of a.hi
+  r = __fsub_rn(r, p.lo);
+  r = __fadd_rn(r, a.lo);
+  r = fmaf(-q1, b.lo, r);
+  float q2 = __fdiv_rn(r, b.hi);
+  return two_sum(q1, q2);
+}
+
+// --------------------------------------------------------- radix-R DFTs
+// DIR = -1: forward, exp(-2 pi i kn/R); DIR = +1: inverse (no 1/R).
+// Output in natural order, in place.
+template <int DIR> DC_DEV void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int DIR> DC_DEV void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  float2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
+  float2 t2 = cadd(v1, v3), t3 = mul_i<DIR>(csub(v1, v3));
+  v0 = cadd(t0, t2);
+  v2 = csub(t0, t2);
+  v1 = cadd(t1, t3);
+  v3 = csub(t1, t3);
+}
+
+// cos and sin of 2 pi m / 16, m = 0..15
+__device__ __constant__ static const float kC16[16] = {
+    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+
+// exp(DIR * 2 pi i m / 16) for a compile-time m (folded by the compiler)
+template <int DIR, int M> DC_DEV float2 w16() {
+  constexpr int m = ((M % 16) + 16) % 16;
+  constexpr float c[16] = {
+      1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+      0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+      -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+      0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+  constexpr float cs = c[m];
+  constexpr float sn = c[(m + 12) % 16];    // sin(x) = cos(x - pi/2)
+  return make_float2(cs, DIR < 0 ? -sn : sn);
+}
+
+template <int DIR, int M> DC_DEV float2 tw16(float2 a) {
+  constexpr int m = ((M % 16) + 16) % 16;
+  if constexpr (m == 0) return a;
+  else if constexpr (m == 4) return mul_i<DIR>(a);
+  else if constexpr (m == 8) return make_float2(-a.x, -a.y);
+  else if constexpr (m == 12) return mul_i<-DIR>(a);
+  else return cmul(a, w16<DIR, M>());
+}
+
+template <int DIR> DC_DEV void dft8(float2 (&v)[8]) {
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<DIR>(e0, e1, e2, e3);
+  dft4<DIR>(o0, o1, o2, o3);
+  o1 = tw16<DIR, 2>(o1);
+  o2 = tw16<DIR, 4>(o2);
+  o3 = tw16<DIR, 6>(o3);
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <int DIR> DC_DEV void dft16(float2 (&v)[16]) {
+  // 16 = 4 x 4: columns n2 (stride 4 in n), twiddle W16^(n2 k1), rows.
+  float2 a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 x0 = v[n2], x1 = v[n2 + 4], x2 = v[n2 + 8], x3 = v[n2 + 12];
+    dft4<DIR>(x0, x1, x2, x3);
+    a[n2][0] = x0; a[n2][1] = x1; a[n2][2] = x2; a[n2][3] = x3;
+  }
+  a[1][1] = tw16<DIR, 1>(a[1][1]);
+  a[1][2] = tw16<DIR, 2>(a[1][2]);
+  a[1][3] = tw16<DIR, 3>(a[1][3]);
+  a[2][1] = tw16<DIR, 2>(a[2][1]);
+  a[2][2] = tw16<DIR, 4>(a[2][2]);
+  a[2][3] = tw16<DIR, 6>(a[2][3]);
+  a[3][1] = tw16<DIR, 3>(a[3][1]);
+  a[3][2] = tw16<DIR, 6>(a[3][2]);
+  a[3][3] = tw16<DIR, 9>(a[3][3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 x0 = a[0][k1], x1 = a[1][k1], x2 = a[2][k1], x3 = a[3][k1];
+    dft4<DIR>(x0, x1, x2, x3);
+    v[k1] = x0; v[k1 + 4] = x1; v[k1 + 8] = x2; v[k1 + 12] = x3;
+  }
+}
+
+template <int R, int DIR> DC_DEV void dft(float2 (&v)[R]) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<DIR>(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    dft8<DIR>(v);
+  } else {
+    static_assert(R == 16, "radix must be 1, 2, 4, 8 or 16");
+    dft16<DIR>(v);
+  }
+}
+
+// --------------------------------------------------------------- twiddles
+// One device table of roots of unity, filled once per context in FP64 on the
+// host and rounded to float:
+//   [0, 4096)        W4096^t = exp(-2 pi i t / 4096)
+//   [4096, 5120)     W(2^20)^j        j in [0, 1024)
+//   [5120, 6144)     W(2^20)^(1024 i) i in [0, 1024)
+// W_M^t for M | 4096 is W4096^(t 4096/M); W_L^t for L | 2^20 is
+// W(2^20)^s with s = t 2^20/L, split as s = 1024 i + j.
+constexpr int kTwMax = 4096;
+constexpr int kTwLo = 4096;
+constexpr int kTwHi = 5120;
+constexpr int kTwSize = 6144;
+constexpr int kLog2Big = 20;
+
+template <int DIR> DC_DEV float2 tw_m(const float2* __restrict__ tw, int t4096) {
+  return conj_if<DIR>(__ldg(tw + t4096));
+}
+// W_L^e for the four-step, e in [0, L), L = 2^log2L <= 2^20
+template <int DIR> DC_DEV float2 tw_big(const float2* __restrict__ tw, uint32_t e, int log2L) {
+  uint32_t s = e << (kLog2Big - log2L);
+  float2 w = cmul(__ldg(tw + kTwHi + (s >> 10)), __ldg(tw + kTwLo + (s & 1023u)));
+  return conj_if<DIR>(w);
+}
+
+}  // namespace dc

@@ -1,0 +1,370 @@
+// Windowed and exact Whittaker-Shannon resampling kernels (Eq. 17, Sec. III-B).
+//
+// Windowed: y[n] = sum_i x[i] h(alpha n - i), h(u) = sinc(u) w(u), w a Kaiser
+// window of half width R, support |u| < R, x zero outside [0, N).  With
+// alpha n = n + delta n = m + e (e in [0,1)) the sum runs over i = m + k,
+// k = -R+1..R, and sinc(e - k) = (-1)^k sin(pi e) / (pi (e - k)).
+//
+// Two kernels:
+//  * direct (any alpha): one output per thread, every weight evaluated.  This
+//    is the paper's Algorithm 1 shape and the library's general path.
+//  * tiled (|alpha - 1| <= 0.01, 32 taps): a CTA owns 1024 consecutive outputs;
+//    its input window is staged in shared memory by one TMA bulk copy; each
+//    warp owns 128 outputs; when e moves by at most 0.015 of a sample across
+//    them (|alpha - 1| <= 1.1e-4, i.e. |v_r| <= 17 km/s) each tap weight is
+//    the quadratic through its exact values at the warp tile's first, middle
+//    and last output (error <= 2e-7; 2e-8 at |v_r| <= 8 km/s).  Other warp
+//    tiles, and tiles where floor(delta n) steps, use exact per-output weights
+//    read against the same staged window.
+#include "resample.cuh"
+
+namespace dc {
+
+constexpr float kInvPi = 0.318309886183790672f;
+constexpr int kRsThreads = 256;
+
+// delta * fi = fl + e with fl integer and e in [0, 1), fi a float holding an
+// integer or half-integer output position (exact), delta a double-float.
+DC_DEV void rs_delay(float dl_hi, float dl_lo, float fi, int& fl, float& e) {
+  df p = two_prod(dl_hi, fi);
+  const float lo = fmaf(dl_lo, fi, p.lo);
+  float f = floorf(p.hi);
+  float r = __fadd_rn(__fsub_rn(p.hi, f), lo);      // p.hi - f is exact
+  if (r < 0.f) {
+    r = __fadd_rn(r, 1.f);
+    f -= 1.f;
+    if (r >= 1.f) { r = 0.f; f += 1.f; }
+  } else if (r >= 1.f) {
+    r = __fsub_rn(r, 1.f);
+    f += 1.f;
+  }
+  fl = (int)f;
+  e = r;
+}
+
+DC_DEV float kaiser_w(const RsArgs& a, float u) {
+  const float z = fmaxf(fmaf(-u * u, a.inv_r2, 1.0f), 0.0f);
+  float w = a.kc[a.nk - 1];
+  for (int j = a.nk - 2; j >= 0; --j) w = fmaf(w, z, a.kc[j]);
+  return w;
+}
+
+// h(e - k) for tap k; s_e = sin(pi e)/pi.
+DC_DEV float tap_weight(const RsArgs& a, float e, float s_e, int k) {
+  const float u = e - (float)k;
+  if (u == 0.f) return 1.f;
+  const float sc = __fdividef((k & 1) ? -s_e : s_e, u);
+  return sc * kaiser_w(a, u);
+}
+
+DC_DEV int find_item(const RsArgs& a, int tile) {
+  int lo = 0, hi = a.n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.items[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------- direct
+__global__ void __launch_bounds__(kRsThreads) resample_direct_kernel(RsArgs a) {
+  const int tile = blockIdx.x;
+  const RsItem& I = a.items[find_item(a, tile)];
+  const int o0 = (tile - I.tile_begin) * kRsTile;
+  for (int q = 0; q < kRsTile / kRsThreads; ++q) {
+    const int i = o0 + q * kRsThreads + threadIdx.x;
+    if (i >= I.n_out) break;
+    int fl;
+    float e;
+    rs_delay(I.dl_hi, I.dl_lo, (float)i, fl, e);
+    const int m = i + fl;
+    float2 acc = make_float2(0.f, 0.f);
+    if (e == 0.f) {
+      if (m >= 0 && m < I.n_in) acc = __ldg(I.x + m);
+    } else {
+      const float s_e = sinpif(e) * kInvPi;
+      for (int k = -a.half + 1; k <= a.half; ++k) {
+        const int idx = m + k;
+        if ((unsigned)idx >= (unsigned)I.n_in) continue;
+        const float h = tap_weight(a, e, s_e, k);
+        const float2 v = __ldg(I.x + idx);
+        acc.x = fmaf(v.x, h, acc.x);
+        acc.y = fmaf(v.y, h, acc.y);
+      }
+    }
+    I.y[i] = acc;
+  }
+}
+
+// ------------------------------------------------------------- tiled
+DC_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+DC_DEV int wpad(int i) { return i + (i >> 2); }   // 4 consecutive outputs per lane
+
+constexpr int kRsQ = 4;                  // consecutive outputs per lane
+constexpr int kRsW = 32 * kRsQ;          // outputs per warp tile
+constexpr int kWaitLimit = 1 << 22;      // bounded mbarrier polls
+// Largest move of e across a warp tile for the quadratic weights: the
+// interpolation error is about 0.064 |h'''| (span/2)^3 <= 2e-7 per weight.
+constexpr float kQuadSpan = 0.015f;
+
+template <int HALF>
+__global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
+  constexpr int TAPS = 2 * HALF;
+  constexpr int NW = kRsThreads / 32;
+  constexpr int WINMAX = kRsTile + 2 * HALF + 40;
+  __shared__ __align__(16) float2 stage[WINMAX + 2];
+  __shared__ float2 win[WINMAX + WINMAX / 4 + 2];
+  __shared__ float4 wts[NW][TAPS];
+  __shared__ __align__(8) unsigned long long mbar;
+
+  const int tile = blockIdx.x;
+  const RsItem& I = a.items[find_item(a, tile)];
+  const int o0 = (tile - I.tile_begin) * kRsTile;
+
+  // Input window of the CTA's 1024 outputs.
+  int flA, flB;
+  float eA, eB;
+  rs_delay(I.dl_hi, I.dl_lo, (float)o0, flA, eA);
+  rs_delay(I.dl_hi, I.dl_lo, (float)(o0 + kRsTile - 1), flB, eB);
+  const int flmin = min(flA, flB) - 2, flmax = max(flA, flB) + 2;
+  const int wlo = o0 + flmin - HALF + 1;
+  const int whi = o0 + kRsTile - 1 + flmax + HALF;
+  const int wlen = whi - wlo + 1;
+  if (wlen > WINMAX) {                       // |delta| outside the tiled range
+    if (threadIdx.x == 0) atomicExch(a.err, 2);
+    return;
+  }
+
+  // TMA bulk copy of the 16-byte-aligned interior of the valid part.
+  const int vlo = max(wlo, 0), vhi = min(whi, I.n_in - 1);
+  int t0 = vlo, t1 = vhi + 1;
+  if (t1 > t0 && (reinterpret_cast<uintptr_t>(I.x + t0) & 15)) ++t0;
+  if (t1 > t0 && ((t1 - t0) & 1)) --t1;
+  if (t1 < t0) t1 = t0;
+  const int sh = (t0 - wlo) & 1;
+  const uint32_t bytes = (uint32_t)(t1 - t0) * 8u;
+  if (bytes) {
+    const uint32_t mb = smem_u32(&mbar);
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(stage + (t0 - wlo + sh))),
+          "l"(I.x + t0), "r"(bytes), "r"(mb)
+          : "memory");
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(mb)
+          : "memory");
+    }
+    if (!done) {
+      atomicExch(a.err, 1);
+      for (int it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mb)
+            : "memory");
+      }
+      return;
+    }
+  }
+  // Repack into the bank-spread layout; zero outside [0, N); ragged edges by
+  // plain loads.
+  for (int idx = threadIdx.x; idx < wlen; idx += kRsThreads) {
+    const int gi = wlo + idx;
+    float2 v = make_float2(0.f, 0.f);
+    if (gi >= t0 && gi < t1) v = stage[idx + sh];
+    else if (gi >= 0 && gi < I.n_in) v = __ldg(I.x + gi);
+    win[wpad(idx)] = v;
+  }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ow = o0 + warp * kRsW;
+  if (ow >= I.n_out) return;
+  constexpr float H = 0.5f * (kRsW - 1);
+  int f0, f1, f2;
+  float e0, e1, e2;
+  rs_delay(I.dl_hi, I.dl_lo, (float)ow, f0, e0);
+  rs_delay(I.dl_hi, I.dl_lo, (float)ow + H, f1, e1);
+  rs_delay(I.dl_hi, I.dl_lo, (float)(ow + kRsW - 1), f2, e2);
+  float2 acc[kRsQ];
+#pragma unroll
+  for (int q = 0; q < kRsQ; ++q) acc[q] = make_float2(0.f, 0.f);
+
+  if (f0 == f2 && f0 == f1 && fabsf(e2 - e0) <= kQuadSpan) {
+    // Quadratic weights per tap through the three nodes s = -H, 0, +H.
+    const float s0 = sinpif(e0) * kInvPi, s1 = sinpif(e1) * kInvPi, s2 = sinpif(e2) * kInvPi;
+    for (int t = lane; t < TAPS; t += 32) {
+      const int k = t - HALF + 1;
+      const float hA = tap_weight(a, e0, s0, k);
+      const float hB = tap_weight(a, e1, s1, k);
+      const float hC = tap_weight(a, e2, s2, k);
+      const float q1 = (hC - hA) * (0.5f / H);
+      const float q2 = (hC - 2.f * hB + hA) * (0.5f / (H * H));
+      wts[warp][t] = make_float4(hB, q1, q2, 0.f);
+    }
+    __syncwarp();
+    const int base = ow + lane * kRsQ + f0 - HALF + 1 - wlo;
+    float sq[kRsQ];
+    float2 xw[kRsQ];
+#pragma unroll
+    for (int q = 0; q < kRsQ; ++q) {
+      sq[q] = (float)(lane * kRsQ + q) - H;
+      xw[q] = win[wpad(base + q)];
+    }
+#pragma unroll
+    for (int t = 0; t < TAPS; ++t) {
+      const float4 w = wts[warp][t];
+#pragma unroll
+      for (int q = 0; q < kRsQ; ++q) {
+        const float h = fmaf(fmaf(w.z, sq[q], w.y), sq[q], w.x);
+        acc[q].x = fmaf(xw[q].x, h, acc[q].x);
+        acc[q].y = fmaf(xw[q].y, h, acc[q].y);
+      }
+#pragma unroll
+      for (int q = 0; q + 1 < kRsQ; ++q) xw[q] = xw[q + 1];
+      if (t + 1 < TAPS) xw[kRsQ - 1] = win[wpad(base + kRsQ + t)];
+    }
+  } else {
+    // floor(delta n) steps inside this warp tile: exact weights per output.
+#pragma unroll 1
+    for (int q = 0; q < kRsQ; ++q) {
+      const int i = ow + lane * kRsQ + q;
+      int fl;
+      float e;
+      rs_delay(I.dl_hi, I.dl_lo, (float)i, fl, e);
+      const int m = i + fl - wlo;
+      if (e == 0.f) {
+        acc[q] = win[wpad(m)];
+      } else {
+        const float s_e = sinpif(e) * kInvPi;
+        for (int k = -HALF + 1; k <= HALF; ++k) {
+          const float h = tap_weight(a, e, s_e, k);
+          const float2 v = win[wpad(m + k)];
+          acc[q].x = fmaf(v.x, h, acc[q].x);
+          acc[q].y = fmaf(v.y, h, acc[q].y);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kRsQ; ++q) {
+    const int i = ow + lane * kRsQ + q;
+    if (i < I.n_out) I.y[i] = acc[q];
+  }
+}
+
+cudaError_t launch_resample_tiled32(const RsArgs& a, cudaStream_t s) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  resample_tiled_kernel<16><<<a.n_tiles, kRsThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resample_direct(const RsArgs& a, cudaStream_t s) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  resample_direct_kernel<<<a.n_tiles, kRsThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- exact sinc, FP32 cores
+// Y[p][n] = sum_m X[p][m] S[n][m], S[n][m] = sinc(alpha n - m)
+//         = (-1)^(m + m_n) sin(pi e_n) / (pi ((m_n - m) + e_n)),  alpha n = m_n + e_n.
+// CTA tile: 64 outputs x 32 pulses, K chunks of 32 samples; S generated in
+// shared memory per chunk and reused by all 32 pulses.
+constexpr int kExBN = 64, kExBP = 32, kExBK = 32;
+
+__global__ void __launch_bounds__(256) exact_fp32_kernel(ExArgs a) {
+  const ExItem& I = a.items[blockIdx.z];
+  const int n0 = blockIdx.x * kExBN, p0 = blockIdx.y * kExBP;
+  __shared__ float Ss[kExBK][kExBN + 4];
+  __shared__ float2 Xs[kExBK][kExBP + 1];
+  __shared__ float sig[kExBN], en[kExBN];
+  __shared__ int mn[kExBN];
+  const int tid = threadIdx.x;
+  if (tid < kExBN) {
+    const int n = n0 + tid;
+    int fl;
+    float e;
+    rs_delay(I.dl_hi, I.dl_lo, (float)n, fl, e);
+    const int m = n + fl;
+    mn[tid] = m;
+    en[tid] = e;
+    const float s = sinpif(e) * kInvPi;
+    sig[tid] = (m & 1) ? -s : s;
+  }
+  const int tn = tid & 15, tp = tid >> 4;        // 4 outputs x 2 pulses per thread
+  float2 acc[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  for (int m0 = 0; m0 < a.n_in; m0 += kExBK) {
+    for (int idx = tid; idx < kExBK * kExBN; idx += 256) {
+      const int n = idx % kExBN, k = idx / kExBN;
+      const int m = m0 + k;
+      float v = 0.f;
+      if (m < a.n_in) {
+        if (en[n] == 0.f) {
+          v = (m == mn[n]) ? 1.f : 0.f;
+        } else {
+          const float den = (float)(mn[n] - m) + en[n];
+          v = __fdividef((m & 1) ? -sig[n] : sig[n], den);
+        }
+      }
+      Ss[k][n] = v;
+    }
+    for (int idx = tid; idx < kExBK * kExBP; idx += 256) {
+      const int k = idx % kExBK, p = idx / kExBK;
+      const int m = m0 + k, pp = p0 + p;
+      Xs[k][p] = (m < a.n_in && pp < a.n_pulses) ? __ldg(I.x + (size_t)pp * a.n_in + m)
+                                                  : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kExBK; ++k) {
+      const float4 s4 = *reinterpret_cast<const float4*>(&Ss[k][tn * 4]);
+      const float2 x0 = Xs[k][tp * 2], x1 = Xs[k][tp * 2 + 1];
+      const float s[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0].x = fmaf(x0.x, s[i], acc[i][0].x);
+        acc[i][0].y = fmaf(x0.y, s[i], acc[i][0].y);
+        acc[i][1].x = fmaf(x1.x, s[i], acc[i][1].x);
+        acc[i][1].y = fmaf(x1.y, s[i], acc[i][1].y);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = n0 + tn * 4 + i;
+    if (n >= a.n_out) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int p = p0 + tp * 2 + j;
+      if (p < a.n_pulses) I.y[(size_t)p * a.n_out + n] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_exact_fp32(const ExArgs& a, int n_alpha, cudaStream_t s) {
+  if (n_alpha <= 0 || a.n_out <= 0 || a.n_pulses <= 0) return cudaSuccess;
+  dim3 grid((a.n_out + kExBN - 1) / kExBN, (a.n_pulses + kExBP - 1) / kExBP, n_alpha);
+  exact_fp32_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dc

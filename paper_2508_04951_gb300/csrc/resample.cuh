@@ -1,0 +1,50 @@
+// Doppler resampling y[n] = x(alpha n Ts) (Eq. 2) by windowed and exact
+// Whittaker-Shannon interpolation (Eq. 17; Sec. III-B; Table I).
+#pragma once
+
+#include "common.cuh"
+
+namespace dc {
+
+constexpr int kMaxKaiser = 40;    // Kaiser I0 polynomial coefficients
+constexpr int kMaxHalf = 32;      // taps <= 64
+
+// One pulse of a windowed-resample launch.
+struct RsItem {
+  const float2* x;     // input samples [n_in]
+  float2* y;           // output samples [n_out]
+  int n_in, n_out;
+  float dl_hi, dl_lo;  // delta = alpha - 1 as a double-float
+  int tile_begin;      // first 1024-output tile of this item in the launch
+};
+
+struct RsArgs {
+  const RsItem* items;
+  int n_items;
+  int n_tiles;         // total tiles of the launch
+  int half;            // R = taps / 2
+  int nk;              // Kaiser coefficients used
+  float inv_r2;        // 1 / R^2
+  float kc[kMaxKaiser];// w(u) = sum_j kc[j] zeta^j, zeta = 1 - (u/R)^2 (I0 series / I0(beta))
+  int* err;            // device error flag (bounded waits)
+};
+
+// One alpha of an exact-sinc launch (config: n_pulses pulses share alpha).
+struct ExItem {
+  const float2* x;     // [n_pulses][n_in]
+  float2* y;           // [n_pulses][n_out]
+  float dl_hi, dl_lo;
+};
+struct ExArgs {
+  const ExItem* items; // one per alpha (grid.z)
+  int n_in, n_out, n_pulses;
+};
+
+constexpr int kRsTile = 1024;     // outputs per CTA of the tiled kernel
+constexpr float kRsTiledMaxDelta = 0.01f;
+
+cudaError_t launch_resample_tiled32(const RsArgs& a, cudaStream_t s);
+cudaError_t launch_resample_direct(const RsArgs& a, cudaStream_t s);
+cudaError_t launch_exact_fp32(const ExArgs& a, int n_alpha, cudaStream_t s);
+
+}  // namespace dc

@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Tolerance: relative L2 error <= 1e-5 per pulse for the FP32 paths (windowed
+resampling, exact FP32 resampling, the FFT correction); bitwise where the
+method is exact (alpha = 1 identity, a pulse alone vs inside a batch).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def dcg():
+    import paper_2508_04951_gb300 as m
+    m.build.build()
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(dcg):
+    c = dcg.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex64)).to("cuda:0")
+
+
+def empty(n):
+    import torch
+    return torch.full((n,), complex(7.0, -7.0), dtype=torch.complex64, device="cuda:0")
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def noise(n, salt):
+    return synth.bandlimited_noise(n, synth.rng_for(1, salt=salt)).astype(np.complex64)
+
+
+# ----------------------------------------------------------- resampling
+
+@pytest.mark.parametrize("n,v,n_out", [
+    (1, 7500.0, 1), (5, -8000.0, 9), (1000, 7500.0, 1000), (4096, -8000.0, 4096),
+    (4097, 8000.0, 2500), (70001, 7500.0, 70001), (70001, -3e5, 70100),
+    (5000, 1.4e6, 5000),              # delta ~ 0.0093: tiled kernel, many wrap tiles
+    (5000, 3e6, 5000),                # delta ~ 0.02: direct kernel
+    (3000, -2e7, 3300),               # alpha ~ 0.875
+])
+def test_windowed_resample_matches_oracle(dcg, ctx, n, v, n_out):
+    x = noise(n, salt=n % 97)
+    xd, yd = to_dev(x), empty(n_out)
+    dcg.doppler_resample(ctx, xd, yd, 20e6, 1e9, v, n_out=n_out)
+    dcg.dc_check(ctx)
+    ref = oracle.resample_windowed(x.astype(np.complex128), oracle.alpha(v), n_out)
+    assert rel(host(yd), ref) <= TOL
+
+
+@pytest.mark.parametrize("taps,beta,v", [(8, 5.0, 7500.0), (16, 8.0, -8000.0), (64, 12.0, 5000.0),
+                                         (32, 3.0, 7000.0)])
+def test_windowed_taps_and_beta(dcg, ctx, taps, beta, v):
+    x = noise(3000, salt=taps)
+    xd, yd = to_dev(x), empty(3000)
+    dcg.doppler_resample(ctx, xd, yd, 20e6, 1e9, v, taps=taps, beta=beta)
+    ref = oracle.resample_windowed(x.astype(np.complex128), oracle.alpha(v), 3000, taps=taps, beta=beta)
+    assert rel(host(yd), ref) <= TOL
+
+
+@pytest.mark.parametrize("taps", [32, 16])
+def test_alpha_one_is_bitwise_identity(dcg, ctx, taps):
+    x = noise(10000, salt=3)
+    xd, yd = to_dev(x), empty(10000)
+    dcg.doppler_resample(ctx, xd, yd, 20e6, 1e9, 0.0, taps=taps)
+    assert np.array_equal(yd.cpu().numpy(), x)
+
+
+def test_lfm_dilated_slope_interior(dcg, ctx):
+    # GPU resampled LFM against the analytic LFM with the dilated slope.
+    cfg = synth.PlainPulse()
+    x = cfg.pulse().astype(np.complex64)
+    xd, yd = to_dev(x), empty(cfg.n)
+    dcg.doppler_resample(ctx, xd, yd, cfg.fs, cfg.fc, cfg.v_r)
+    a = oracle.alpha(cfg.v_r)
+    T = cfg.n / cfg.fs
+    t = a * np.arange(cfg.n) / cfg.fs
+    analytic = np.exp(1j * np.pi * cfg.bandwidth / T * (t - T / 2) ** 2)
+    sl = slice(64, int((cfg.n - 1) / a) - 64)
+    assert np.max(np.abs(host(yd)[sl] - analytic[sl])) < 2e-4
+
+
+@pytest.mark.parametrize("n,n_out,v", [(1000, 1000, 7500.0), (2048, 2100, -8000.0), (1, 3, 100.0),
+                                       (4096, 4096, 7500.0)])
+def test_exact_fp32_matches_oracle(dcg, ctx, n, n_out, v):
+    x = noise(n, salt=11)
+    xd, yd = to_dev(x), empty(n_out)
+    dcg.doppler_resample(ctx, xd, yd, 20e6, 1e9, v, mode=dcg.DC_EXACT_FP32, n_out=n_out)
+    ref = oracle.resample_exact(x.astype(np.complex128), oracle.alpha(v), n_out)
+    assert rel(host(yd), ref) <= TOL
+
+
+def test_exact_fp32_batch_many_alpha(dcg, ctx):
+    import torch
+    n, P, V = 1024, 40, 5
+    X = np.stack([noise(n, salt=100 + p) for p in range(P)])
+    v = np.linspace(-8000, 8000, V)
+    xd = to_dev(X.reshape(-1))
+    yd = torch.empty(V * P * n, dtype=torch.complex64, device="cuda:0")
+    dcg.resample_exact_batch(ctx, xd, n, P, v, yd, mode=dcg.DC_EXACT_FP32)
+    Y = host(yd).reshape(V, P, n)
+    for i in range(V):
+        ref = oracle.resample_exact(X.astype(np.complex128), oracle.alpha(v[i]), n)
+        for p in (0, 17, P - 1):
+            assert rel(Y[i, p], ref[p]) <= TOL
+
+
+# ---------------------------------------------------- ionospheric correction
+
+@pytest.mark.parametrize("n", [1, 2, 3, 100, 4095, 4096, 4097, 8192, 20000, 65536, 200000, 1 << 20])
+@pytest.mark.parametrize("tec", [50.0, -150.0])
+def test_iono_correct_matches_oracle(dcg, ctx, n, tec):
+    x = noise(n, salt=n % 31)
+    xd, yd = to_dev(x), empty(n)
+    dcg.iono_correct(ctx, xd, yd, 20e6, 1e9, tec)
+    dcg.dc_check(ctx)
+    ref = oracle.iono_correct(x.astype(np.complex128), 20e6, 1e9, tec)
+    assert rel(host(yd), ref) <= TOL
+
+
+def test_iono_zero_tec_and_in_place(dcg, ctx):
+    x = noise(30000, salt=5)
+    xd = to_dev(x)
+    dcg.iono_correct(ctx, xd, xd, 20e6, 1e9, 0.0)          # in place, E = 0
+    assert rel(host(xd), x) <= 1e-6
+
+
+def test_iono_rf_sampling_e1(dcg, ctx):
+    # RF-sampled LFM of the Fig. 2 example (fc = 0: bins are RF frequencies).
+    from oracle import predistortion as pdist
+    fs, f0, B, T = 2.048e9, 413e6, 18e6, 100e-6
+    n = int(round(T * fs))
+    t = np.arange(n) / fs
+    x = np.exp(1j * pdist.lfm_phase(t, f0, B, T)).astype(np.complex64)
+    xd, yd = to_dev(x), empty(n)
+    dcg.iono_correct(ctx, xd, yd, fs, 0.0, 100.0)
+    ref = oracle.iono_correct(x.astype(np.complex128), fs, 0.0, 100.0)
+    assert rel(host(yd), ref) <= TOL
+
+
+# ---------------------------------------------------------- full pipeline
+
+def test_plain_pulse_config1_both_modes(dcg, ctx):
+    cfg = synth.PlainPulse()
+    x = cfg.pulse().astype(np.complex64)
+    for mode, name in ((dcg.DC_WINDOWED, "windowed"), (dcg.DC_EXACT_FP32, "exact")):
+        xd, yd, zd = to_dev(x), empty(cfg.n), empty(cfg.n)
+        dcg.doppler_resample(ctx, xd, yd, cfg.fs, cfg.fc, cfg.v_r, mode=mode)
+        dcg.iono_correct(ctx, yd, zd, cfg.fs, cfg.fc, cfg.tec)
+        ref = oracle.correct(x.astype(np.complex128), cfg.fs, cfg.fc, cfg.v_r, cfg.tec, mode=name)
+        assert rel(host(zd), ref) <= TOL, name
+
+
+def _ragged_batch(lengths, seed):
+    rng = np.random.default_rng(seed)
+    items = np.zeros(len(lengths), dtype=__import__("paper_2508_04951_gb300").ITEM_DTYPE)
+    xs, off, ooff = [], 0, 0
+    for i, n in enumerate(lengths):
+        n_out = int(n if i % 3 else max(1, n + rng.integers(-n // 4 - 1, n // 4 + 2)))
+        x = noise(n, salt=200 + i)
+        xs.append(x)
+        items[i] = (off, n, ooff, n_out, 20e6, 1e9, rng.uniform(-8000, 8000), rng.uniform(5, 150))
+        off += n
+        ooff += n_out
+    return items, np.concatenate(xs), ooff
+
+
+LENGTHS = [1, 3, 17, 1000, 1024, 1500, 4096, 4097, 9000, 16384, 40000, 65536, 100000, 262144]
+
+
+def test_correct_batch_ragged_matches_oracle(dcg, ctx):
+    items, x, total_out = _ragged_batch(LENGTHS, 1)
+    xd, od = to_dev(x), empty(total_out)
+    dcg.correct_batch(ctx, xd, od, items)
+    dcg.dc_check(ctx)
+    out = host(od)
+    for it in items:
+        xi = x[it["in_off"]:it["in_off"] + it["n"]].astype(np.complex128)
+        ref = oracle.correct(xi, it["fs"], it["fc"], it["v_r"], it["tec_tecu"], n_out=int(it["n_out"]))
+        got = out[it["out_off"]:it["out_off"] + it["n_out"]]
+        assert rel(got, ref) <= TOL, (it["n"], it["n_out"])
+
+
+def test_batch_result_independent_of_batch(dcg, ctx):
+    items, x, total_out = _ragged_batch(LENGTHS, 2)
+    xd, od = to_dev(x), empty(total_out)
+    dcg.correct_batch(ctx, xd, od, items)
+    mixed = od.cpu().numpy()
+    for j in (0, 5, 7, 13):
+        one = items[j:j + 1].copy()
+        one["out_off"] = 0
+        alone = empty(int(one["n_out"][0]))
+        dcg.correct_batch(ctx, xd, alone, one)
+        o0 = int(items[j]["out_off"])
+        assert np.array_equal(alone.cpu().numpy(), mixed[o0:o0 + int(items[j]["n_out"])])
+
+
+def test_correct_batch_exact_mode(dcg, ctx):
+    items, x, total_out = _ragged_batch([700, 2048, 3000], 3)
+    xd, od = to_dev(x), empty(total_out)
+    dcg.correct_batch(ctx, xd, od, items, mode=dcg.DC_EXACT_FP32)
+    out = host(od)
+    for it in items:
+        xi = x[it["in_off"]:it["in_off"] + it["n"]].astype(np.complex128)
+        ref = oracle.correct(xi, it["fs"], it["fc"], it["v_r"], it["tec_tecu"], mode="exact",
+                             n_out=int(it["n_out"]))
+        assert rel(out[it["out_off"]:it["out_off"] + it["n_out"]], ref) <= TOL
+
+
+@pytest.mark.parametrize("n,n_v,n_tec", [(3000, 5, 3), (4096, 3, 2), (65536, 4, 3), (70000, 2, 2)])
+def test_correct_bank_matches_oracle(dcg, ctx, n, n_v, n_tec):
+    import torch
+    x = noise(n, salt=n % 13)
+    rng = np.random.default_rng(n)
+    v = rng.uniform(-8000, 8000, n_v)
+    tec = rng.uniform(5, 150, n_tec)
+    od = torch.empty(n_v * n_tec * n, dtype=torch.complex64, device="cuda:0")
+    dcg.correct_bank(ctx, to_dev(x), v, tec, od, 20e6, 1e9)
+    dcg.dc_check(ctx)
+    out = host(od).reshape(n_v, n_tec, n)
+    ref = oracle.correct_bank(x.astype(np.complex128), 20e6, 1e9, v, tec)
+    for i in range(n_v):
+        for t in range(n_tec):
+            assert rel(out[i, t], ref[i, t]) <= TOL
+
+
+def test_correct_bank_full_size_sampled(dcg, ctx):
+    # The Doppler-bank workload at full size, in the launch configuration the
+    # benchmark times; sampled (v_r, TEC) pairs checked whole against the oracle.
+    import torch
+    cfg = synth.DopplerBank()
+    x, v, tec = cfg.draw()
+    x = x.astype(np.complex64)
+    od = torch.empty(cfg.n_v * cfg.n_tec * cfg.n, dtype=torch.complex64, device="cuda:0")
+    dcg.correct_bank(ctx, to_dev(x), v, tec, od, cfg.fs, cfg.fc)
+    dcg.dc_check(ctx)
+    out = od.view(cfg.n_v, cfg.n_tec, cfg.n)
+    rng = np.random.default_rng(9)
+    pairs = [(0, 0), (cfg.n_v - 1, cfg.n_tec - 1)] + [tuple(p) for p in
+                                                     zip(rng.integers(0, cfg.n_v, 4), rng.integers(0, cfg.n_tec, 4))]
+    x64 = x.astype(np.complex128)
+    for i, t in pairs:
+        ref = oracle.correct(x64, cfg.fs, cfg.fc, v[i], tec[t])
+        assert rel(out[i, t].cpu().numpy(), ref) <= TOL, (i, t)
+    del od
+
+
+# ------------------------------------------------------------- validation
+
+def test_invalid_arguments_launch_nothing(dcg, ctx):
+    x = to_dev(noise(64, salt=1))
+    y = empty(64)
+    bad = [
+        dict(fs=20e6, fc=5e6, v_r=0.0),           # 0 < fc <= fs/2
+        dict(fs=-1.0, fc=1e9, v_r=0.0),
+        dict(fs=20e6, fc=1e9, v_r=3e8),           # |v_r| >= c
+    ]
+    for kw in bad:
+        with pytest.raises(dcg.DcError) as e:
+            dcg.doppler_resample(ctx, x, y, kw["fs"], kw["fc"], kw["v_r"])
+        assert e.value.status == 1
+    with pytest.raises(dcg.DcError):
+        dcg.doppler_resample(ctx, x, y, 20e6, 1e9, 0.0, taps=31)
+    with pytest.raises(dcg.DcError):
+        dcg.doppler_resample(ctx, x, y, 20e6, 1e9, 0.0, n_out=(1 << 20) + 1)
+    with pytest.raises(dcg.DcError):
+        dcg.iono_correct(ctx, x, y, 20e6, 1e9, float("nan"))
+    dcg.dc_check(ctx)
+    assert np.all(y.cpu().numpy() == np.complex64(7 - 7j))
