@@ -181,6 +181,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
     cfg = synth.DopplerBank()
+    if args.n_v:
+        cfg.n_v = args.n_v
     x, v, tec = cfg.draw()
     x32 = x.astype(np.complex64)
     ctx = dcg.Context(local_rank)
@@ -333,6 +335,7 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample-v", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-v", type=int, default=None, help="fewer range rates (small profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
