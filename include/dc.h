@@ -142,6 +142,35 @@ DC_API dc_status doppler_resample(dc_ctx* ctx, const dc_c64* x_dev, long long n,
 DC_API dc_status iono_correct(dc_ctx* ctx, const dc_c64* x_dev, long long n, dc_c64* y_dev,
                        double fs, double fc, double tec_tecu, void* stream);
 
+/* Ionospheric correction with no device allocation at run time.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that are not allowed to allocate device memory while they run: for example
+ * a real-time receive loop with a fixed memory plan, where cudaMalloc could
+ * stall the pipeline (it may synchronise the device), or a host application
+ * whose device memory is all owned by its own pool allocator.  Such callers
+ * cannot create a dc_ctx (which allocates tables and scratch), so this call
+ * needs no context at all.
+ *
+ * Same computation and arguments as iono_correct (x_dev, y_dev: [n], in place
+ * allowed), limited to 1 <= n <= 262144 (2^18) samples; a larger n, or any
+ * argument iono_correct would reject, returns DC_EINVAL without launching.
+ * The four-step scratch (2 MiB), the twiddle tables and the launch
+ * descriptors are fixed-size __device__ arrays inside libdc.so: every GPU that
+ * loads the library keeps them until the process exits, and this call never
+ * calls cudaMalloc or cudaFree.  Runs on the current CUDA device.
+ *
+ * The first call on a device sets up that device: it resolves the arrays'
+ * device addresses (cudaGetSymbolAddress, with the device current) and writes
+ * the twiddle tables with a synchronous copy.  Make that first call before
+ * any stream capture.  All calls share the one scratch array and descriptor
+ * slots, which keep the last call's contents (the scratch is fully rewritten
+ * before it is read, so nothing needs clearing); calls whose work overlaps on
+ * the GPU -- on different streams, say -- race with each other, so issue them
+ * on one stream or serialise them.  DC_ECUDA on a CUDA runtime error. */
+DC_API dc_status iono_correct_noalloc(const dc_c64* x_dev, long long n, dc_c64* y_dev,
+                                      double fs, double fc, double tec_tecu, void* stream);
+
 /* One pulse of a batch.  Offsets and lengths count complex samples. */
 typedef struct {
   long long in_off;     /* first input sample in in_dev                      */

@@ -23,7 +23,7 @@ __all__ = [
     "DcError", "Context", "load", "lib_path",
     "DC_WINDOWED", "DC_EXACT_FP32", "DC_EXACT_BF16X3", "DC_EXACT_FP16X3",
     "ITEM_DTYPE", "dc_opts_default", "dc_check", "dc_launch_count", "dc_profile_enable",
-    "dc_profile_read", "doppler_resample", "iono_correct",
+    "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc",
     "correct_batch", "correct_bank", "resample_exact_batch", "exported_symbols",
 ]
 
@@ -86,6 +86,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "dc_profile_read": (i, [vp, ctypes.POINTER(DcPhaseTime), i]),
         "doppler_resample": (i, [vp, vp, ll, vp, d, d, d, ctypes.POINTER(DcOpts), vp]),
         "iono_correct": (i, [vp, vp, ll, vp, d, d, d, vp]),
+        "iono_correct_noalloc": (i, [vp, ll, vp, d, d, d, vp]),
         "correct_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), vp]),
         "correct_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts), vp]),
         "resample_exact_batch": (i, [vp, vp, ll, i, ll, dp, i, vp, ll, i, vp]),
@@ -101,7 +102,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     """Names of the C entry points this binding binds (all declared in dc.h)."""
     return ["dc_opts_default", "dc_status_str", "dc_create", "dc_destroy", "dc_last_error",
-            "dc_check", "dc_launch_count", "dc_profile_enable", "dc_profile_read", "doppler_resample", "iono_correct", "correct_batch", "correct_bank",
+            "dc_check", "dc_launch_count", "dc_profile_enable", "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc", "correct_batch", "correct_bank",
             "resample_exact_batch"]
 
 
@@ -208,6 +209,24 @@ def doppler_resample(ctx: Context, x, y, fs: float, fc: float, v_r: float, *, ta
 def iono_correct(ctx: Context, x, y, fs: float, fc: float, tec_tecu: float, *, stream=None) -> None:
     ctx.check(ctx.lib.iono_correct(ctx.handle, _ptr(x), x.numel(), _ptr(y), fs, fc, tec_tecu,
                                    _stream(stream)))
+
+
+NOALLOC_MAX = 1 << 18
+
+
+def iono_correct_noalloc(x, y, fs: float, fc: float, tec_tecu: float, *, stream=None) -> None:
+    """iono_correct without a context and without any device allocation, for
+    callers that may not allocate device memory at run time (fixed-size
+    scratch inside the library; n <= 2^18).  Calls that overlap on the GPU
+    share that scratch, so keep them on one stream."""
+    lib = load()
+    n = x.numel()
+    if n > NOALLOC_MAX:
+        raise DcError(1, f"n = {n} exceeds the {NOALLOC_MAX}-sample static scratch of "
+                         "iono_correct_noalloc; use iono_correct with a Context")
+    st = lib.iono_correct_noalloc(_ptr(x), n, _ptr(y), fs, fc, tec_tecu, _stream(stream))
+    if st:
+        raise DcError(st, "iono_correct_noalloc rejected its arguments or failed")
 
 
 def correct_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_WINDOWED,
