@@ -12,8 +12,10 @@
 
 #include "../../include/dc.h"
 #include "fft.cuh"
+#include "fused.cuh"
 #include "phase.cuh"
 #include "resample.cuh"
+#include "twiddle_host.h"
 
 using namespace dc;
 
@@ -72,10 +74,13 @@ dc_status cuda_fail(dc_ctx* c, cudaError_t e, const char* what) {
 
 // Kernel phases, named in dc_profile_read().
 enum Ph { PH_RS_TILED, PH_RS_DIRECT, PH_EXACT, PH_ROW_FULL, PH_COL_F1, PH_ROW_MID, PH_COL_B,
-          PH_ROW_SPEC, PH_ROW_APPLY, PH_PHASE_TABLE, PH_COUNT };
+          PH_ROW_SPEC, PH_ROW_APPLY, PH_PHASE_TABLE, PH_FUSED_FULL, PH_FUSED_SPEC, PH_FUSED_APPLY,
+          PH_COUNT };
 const char* kPhaseName[PH_COUNT] = {"resample_tiled", "resample_direct", "exact_fp32", "row_full",
                                     "col_f1", "row_mid", "col_b", "row_spec", "row_apply",
-                                    "phase_table"};
+                                    "phase_table", "fused_full", "fused_spec", "fused_apply"};
+// Transform lengths handled by the cluster-fused kernels.
+bool fused_L(int log2L) { return log2L >= 12 && log2L <= 16; }
 
 cudaEvent_t take_event(dc_ctx* c) {
   if (!c->pool.empty()) {
@@ -308,6 +313,18 @@ dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2*
   if (it.empty()) return DC_OK;
   const FftItem* dev = nullptr;
   cudaError_t e;
+  if (fused_L(log2L)) {
+    dc_status st = upload(c, it, item_at, s, &dev);
+    if (st) return st;
+    item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
+    FusedArgs a{dev, (int)it.size(), log2L, c->tw, c->err};
+    long long outs = 0;
+    for (auto& f : it) outs += f.n_out;
+    Phase ph(c, PH_FUSED_FULL, s, outs);
+    e = launch_fused(FUSED_FULL, a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fused launch");
+    return DC_OK;
+  }
   if (log2L <= 12) {
     dc_status st = upload(c, it, item_at, s, &dev);
     if (st) return st;
@@ -402,16 +419,7 @@ dc_status dc_create(dc_ctx** out, int device, size_t budget) {
   c->budget = budget;
   // Twiddle tables in FP64, rounded to float (layout in common.cuh).
   std::vector<float2> tw(kTwSize);
-  for (int t = 0; t < 4096; ++t) {
-    const double a = -2.0 * kPi * t / 4096.0;
-    tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  for (int j = 0; j < 1024; ++j) {
-    const double a = -2.0 * kPi * j / (double)(1 << 20);
-    tw[kTwLo + j] = make_float2((float)std::cos(a), (float)std::sin(a));
-    const double b = -2.0 * kPi * j / 1024.0;
-    tw[kTwHi + j] = make_float2((float)std::cos(b), (float)std::sin(b));
-  }
+  fill_twiddles(tw.data());
   if ((e = cudaMalloc(&c->tw, sizeof(float2) * kTwSize)) != cudaSuccess ||
       (e = cudaMemcpy(c->tw, tw.data(), sizeof(float2) * kTwSize, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
@@ -667,13 +675,20 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
 
 // Phase table for the bank: P[t][k] = exp(-i phi_k(TEC_t)).
 namespace dc {
-__global__ void phase_table_kernel(const PhaseParams* ph, int n_tec, int log2L, float2* P) {
+// fused != 0: the layout of the cluster-fused kernels -- element k1*4096 + k2
+// holds bin k1 + L1 k2 (L1 = L/4096) -- with the inverse transform's 1/L folded in.
+__global__ void phase_table_kernel(const PhaseParams* ph, int n_tec, int log2L, int fused,
+                                   float2* P) {
   const size_t L = (size_t)1 << log2L;
   const size_t total = L * (size_t)n_tec;
+  const int log2L1 = log2L > 12 ? log2L - 12 : 0;
+  const float scale = fused ? 1.0f / (float)L : 1.0f;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
        g += (size_t)gridDim.x * blockDim.x) {
-    const int t = (int)(g >> log2L), k = (int)(g & (L - 1));
-    P[g] = ph[t].enabled ? iono_factor(ph[t], k) : make_float2(1.f, 0.f);
+    const int t = (int)(g >> log2L), idx = (int)(g & (L - 1));
+    const int k = fused ? ((idx >> 12) + ((idx & 4095) << log2L1)) : idx;
+    const float2 w = ph[t].enabled ? iono_factor(ph[t], k) : make_float2(1.f, 0.f);
+    P[g] = cscale(w, scale);
   }
 }
 }  // namespace dc
@@ -708,7 +723,8 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   const size_t y_at = ar.take((size_t)n_v * n_out * sizeof(float2));
   const size_t p_at = ar.take((size_t)n_tec * L * sizeof(float2));
   const size_t s_at = ar.take((size_t)n_v * L * sizeof(float2));
-  const size_t t_at = ar.take((size_t)std::max(chunk, four ? n_v : 0) * L * sizeof(float2));
+  const size_t t_at =
+      ar.take(fused_L(log2L) ? 0 : (size_t)std::max(chunk, four ? n_v : 0) * L * sizeof(float2));
   const size_t ph_at = ar.take((size_t)n_tec * sizeof(PhaseParams));
   if ((st = ensure_ws(c, ar.off))) return st;
   const size_t n_pairs = (size_t)n_v * n_tec;
@@ -732,7 +748,7 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     Phase ph(c, PH_PHASE_TABLE, s, (long long)total);
     phase_table_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const PhaseParams*>(ws + ph_at), n_tec,
-                                             log2L, P);
+                                             log2L, fused_L(log2L) ? 1 : 0, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "phase table launch");
   }
   // 2. resample per v_r
@@ -756,7 +772,14 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     sp[i].n_out = (int)n_out;
   }
   const FftItem* dev = nullptr;
-  if (!four) {
+  const bool fused = fused_L(log2L);
+  if (fused) {
+    if ((st = upload(c, sp, item_at, s, &dev))) return st;
+    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
+    FusedArgs a{dev, n_v, log2L, c->tw, c->err};
+    Phase ph(c, PH_FUSED_SPEC, s, (long long)n_v * n_out);
+    if ((e = launch_fused(FUSED_SPEC, a, s)) != cudaSuccess) return cuda_fail(c, e, "spec launch");
+  } else if (!four) {
     if ((st = upload(c, sp, item_at, s, &dev))) return st;
     item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
     RowArgs a{dev, n_v, log2L, 0, c->tw};
@@ -793,6 +816,13 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
       f.n_valid = (int)n_out;
       f.n_out = (int)n_out;
     }
+  if (fused) {
+    if ((st = upload(c, ap, item_at, s, &dev))) return st;
+    FusedArgs a{dev, (int)n_pairs, log2L, c->tw, c->err};
+    Phase ph(c, PH_FUSED_APPLY, s, (long long)n_pairs * n_out);
+    if ((e = launch_fused(FUSED_APPLY, a, s)) != cudaSuccess) return cuda_fail(c, e, "apply launch");
+    return DC_OK;
+  }
   if (!four) {
     if ((st = upload(c, ap, item_at, s, &dev))) return st;
     RowArgs a{dev, (int)n_pairs, log2L, 0, c->tw};

@@ -79,13 +79,6 @@ template <int DIR> DC_DEV void dft4(float2& v0, float2& v1, float2& v2, float2& 
   v3 = csub(t1, t3);
 }
 
-// cos and sin of 2 pi m / 16, m = 0..15
-__device__ __constant__ static const float kC16[16] = {
-    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
-    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
-
 // exp(DIR * 2 pi i m / 16) for a compile-time m (folded by the compiler)
 template <int DIR, int M> DC_DEV float2 w16() {
   constexpr int m = ((M % 16) + 16) % 16;
@@ -164,16 +157,22 @@ template <int R, int DIR> DC_DEV void dft(float2 (&v)[R]) {
 
 // --------------------------------------------------------------- twiddles
 // One device table of roots of unity, filled once per context in FP64 on the
-// host and rounded to float:
-//   [0, 4096)        W4096^t = exp(-2 pi i t / 4096)
-//   [4096, 5120)     W(2^20)^j        j in [0, 1024)
-//   [5120, 6144)     W(2^20)^(1024 i) i in [0, 1024)
+// host and rounded to float (fill_twiddles in twiddle_host.h):
+//   [0, 4096)          W4096^t = exp(-2 pi i t / 4096)
+//   [4096, 5120)       W(2^20)^j        j in [0, 1024)
+//   [5120, 6144)       W(2^20)^(1024 i) i in [0, 1024)
+//   [6144, 6384)       W256^(r k)   at 6144 + (r-1)*16 + k,  r in [1,16), k in [0,16)
+//   [6384, 10224)      W4096^(r j)  at 6384 + (r-1)*256 + j, r in [1,16), j in [0,256)
 // W_M^t for M | 4096 is W4096^(t 4096/M); W_L^t for L | 2^20 is
-// W(2^20)^s with s = t 2^20/L, split as s = 1024 i + j.
+// W(2^20)^s with s = t 2^20/L, split as s = 1024 i + j.  The last two blocks
+// are the per-stage twiddles of a 4096-point radix-16 row, laid out so a
+// warp's 32 consecutive butterflies read consecutive entries.
 constexpr int kTwMax = 4096;
 constexpr int kTwLo = 4096;
 constexpr int kTwHi = 5120;
-constexpr int kTwSize = 6144;
+constexpr int kTwS2 = 6144;
+constexpr int kTwS3 = 6384;
+constexpr int kTwSize = 10224;
 constexpr int kLog2Big = 20;
 
 template <int DIR> DC_DEV float2 tw_m(const float2* __restrict__ tw, int t4096) {

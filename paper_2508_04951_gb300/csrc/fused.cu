@@ -1,0 +1,268 @@
+// Cluster-fused FFT correction kernels; see fused.cuh for the data flow.
+#include <cooperative_groups.h>
+
+#include "fused.cuh"
+#include "tma.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dc {
+
+namespace {
+
+constexpr int kRowN = 4096;             // row length
+constexpr int kRowThreads = 256;        // threads per row (one radix-16 butterfly each)
+constexpr int kRowPitch = kRowN + kRowN / 16;
+
+DC_DEV int pad16(int p) { return p + (p >> 4); }
+
+// Stage twiddles of a 4096-point row from the precomputed tables:
+// stage 2 multiplies v[r] by W256^(r k), k = j mod 16; stage 3 by W4096^(r j).
+template <int DIR>
+DC_DEV void twiddle_stage2(float2 (&v)[16], const float2* __restrict__ tw, int k) {
+#pragma unroll
+  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], conj_if<DIR>(__ldg(tw + kTwS2 + (r - 1) * 16 + k)));
+}
+template <int DIR>
+DC_DEV void twiddle_stage3(float2 (&v)[16], const float2* __restrict__ tw, int j) {
+#pragma unroll
+  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], conj_if<DIR>(__ldg(tw + kTwS3 + (r - 1) * 256 + j)));
+}
+
+// One 4096-point row, thread j of 256.  In: v[r] = x[j + 256 r].
+// Out: v[r] = X[j + 256 r].  Three radix-16 Stockham stages exchanging
+// through two padded shared-memory buffers (element p at p + p/16): stage 1
+// writes b1, stage 2 reads b1 and writes b2, stage 3 reads b2.  One CTA
+// barrier per exchange; the caller must make sure nobody still reads b1 when
+// this starts.  Every thread of the CTA calls this together.
+template <int DIR>
+DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
+                    const float2* __restrict__ tw) {
+  dft16<DIR>(v);                                           // Ns = 1
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b1[pad16(16 * j + r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b1[pad16(j + 256 * r)];
+  twiddle_stage2<DIR>(v, tw, j & 15);                      // Ns = 16: W256^(r k)
+  dft16<DIR>(v);
+  const int base = (j >> 4) * 256 + (j & 15);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b2[pad16(base + 16 * r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b2[pad16(j + 256 * r)];
+  twiddle_stage3<DIR>(v, tw, j);                           // Ns = 256: W4096^(r j)
+  dft16<DIR>(v);
+}
+
+template <int CL> DC_DEV void cluster_sync() {
+  if constexpr (CL > 1) cg::this_cluster().sync();
+  else __syncthreads();
+}
+// Split cluster barrier: arrive (release: our reads of peers' shared memory
+// are done) as soon as the last remote values are consumed, wait (acquire)
+// only before exiting, so a CTA's shared memory outlives its peers' reads.
+template <int CL> DC_DEV void cluster_arrive() {
+  if constexpr (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+template <int CL> DC_DEV void cluster_wait() {
+  if constexpr (CL > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int CL> DC_DEV float2* row_of(float2* sm, int owner) {
+  if constexpr (CL > 1) return cg::this_cluster().map_shared_rank(sm, owner);
+  else return sm;
+}
+
+// One 4096-point row per CTA; clusters of L1 CTAs (16 at L = 65536, beyond
+// the portable 8).  Register caps give 3 resident CTAs per SM for the
+// spectrum and apply kernels, 2 for the full correction (phase evaluation).
+constexpr int kRowsPerCta = 1;
+
+template <int LOG2L1, int OP>
+__global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 2 : 3)
+    fused_kernel(FusedArgs a) {
+  constexpr int L1 = 1 << LOG2L1;
+  constexpr int ROWS = L1 >= kRowsPerCta ? kRowsPerCta : 1;   // rows per CTA
+  constexpr int CL = L1 / ROWS;              // CTAs per cluster (per transform)
+  constexpr int NT = ROWS * kRowThreads;
+  constexpr int COLS = kRowN / CL;           // columns per CTA in the column passes
+  constexpr int LOG2L = 12 + LOG2L1;
+  extern __shared__ __align__(128) float2 sm[];   // [ROWS][2][kRowPitch]: per row, buffers A and B
+
+  const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int item = blockIdx.x / CL;
+  const FftItem I = a.items[item];
+  const int t = threadIdx.x;
+  const int lr = t >> 8, j = t & 255;
+  const int k1 = rank * ROWS + lr;
+  float2* bufA = sm + (2 * lr) * kRowPitch;
+  float2* bufB = bufA + kRowPitch;
+  float2 v[16];
+
+  // ---------------------------------------------------------- input side
+  if constexpr (OP == FUSED_APPLY) {
+    // spectrum row k1 -> A, phase row k1 -> B (two 32 KiB bulk copies)
+    __shared__ __align__(8) unsigned long long bar;
+    if (t == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (t == 0) {
+      mbar_expect_tx(&bar, 2 * kRowN * sizeof(float2));
+      bulk_g2s(bufA, I.src + (size_t)k1 * kRowN, kRowN * sizeof(float2), &bar);
+      bulk_g2s(bufB, I.ptab + (size_t)k1 * kRowN, kRowN * sizeof(float2), &bar);
+    }
+    mbar_wait_bounded(&bar, 0, a.err);   // on a timeout: flag raised, keep going
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(bufA[j + 256 * r], bufB[j + 256 * r]);
+    __syncthreads();                     // the row FFT overwrites A and B
+  } else if constexpr (LOG2L1 == 0) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int n = j + 256 * r;
+      v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+    }
+  } else {
+    // forward columns (length L1) of this CTA's column range, scattered to the
+    // rows' owners, times W_L^(n2 k1)
+    for (int c = t; c < COLS; c += NT) {
+      const int n2 = rank * COLS + c;
+      float2 col[L1];
+#pragma unroll
+      for (int n1 = 0; n1 < L1; ++n1) {
+        const int n = n2 + kRowN * n1;
+        col[n1] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+      }
+      dft<L1, -1>(col);
+#pragma unroll
+      for (int q = 1; q < L1; ++q) col[q] = cmul(col[q], tw_big<-1>(a.tw, (uint32_t)(n2 * q), LOG2L));
+#pragma unroll
+      for (int q = 0; q < L1; ++q) row_of<CL>(sm, q / ROWS)[(2 * (q % ROWS)) * kRowPitch + pad16(n2)] = col[q];
+    }
+    cluster_sync<CL>();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = bufA[pad16(j + 256 * r)];
+  }
+
+  // ---------------------------------------------------------------- rows
+  // FULL/SPEC: the input sits in A (read above), so the forward row starts in
+  // B; its last exchange is in A, so the inverse row starts in B again.
+  if constexpr (OP == FUSED_FULL || OP == FUSED_SPEC) row4096<-1>(v, bufB, bufA, j, a.tw);
+  if constexpr (OP == FUSED_SPEC) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) I.dst[(size_t)k1 * kRowN + j + 256 * r] = v[r];
+    return;
+  }
+  if constexpr (OP == FUSED_FULL) {
+    const float invL = 1.0f / (float)(1 << LOG2L);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const float2 w = I.ph.enabled ? iono_factor(I.ph, k1 + L1 * (j + 256 * r)) : make_float2(1.f, 0.f);
+      v[r] = cscale(cmul(v[r], w), invL);
+    }
+  }
+  if constexpr (OP == FUSED_FULL) {
+    // B was last read before the forward's second barrier; A (read by the
+    // forward's stage 3) is next written after the inverse's first barrier.
+    row4096<+1>(v, bufB, bufA, j, a.tw);       // result exchanged last through A
+  } else {
+    row4096<+1>(v, bufA, bufB, j, a.tw);       // result exchanged last through B
+  }
+  float2* out_buf = OP == FUSED_FULL ? bufB : bufA; // free: last read before a barrier
+
+  // ------------------------------------------------------------ output side
+  if constexpr (LOG2L1 == 0) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int n = j + 256 * r;
+      if (n < I.n_out) __stcs(I.dst + n, v[r]);
+    }
+    return;
+  } else {
+    // four-step twiddle W_L^(-n2 k1), n2 = j + 256 r:
+    //   = W_L^(-j k1) * W_(16 L1)^(-r k1)   (second factor uniform in the CTA)
+    if (k1) {
+      const float2 a_j = tw_big<+1>(a.tw, (uint32_t)(j * k1), LOG2L);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        // W_(16 L1)^(-r k1) = W4096^(-(r k1 mod 16 L1) * 256 / L1)
+        const int e = ((r * k1) & (16 * L1 - 1)) * (256 / L1);
+        v[r] = cmul(v[r], cmul(a_j, tw_m<+1>(a.tw, e)));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) out_buf[pad16(j + 256 * r)] = v[r];
+    cluster_sync<CL>();
+    const int out_off = OP == FUSED_FULL ? kRowPitch : 0;   // buffer B or A of each row
+    for (int c = t; c < COLS; c += NT) {
+      const int n2 = rank * COLS + c;
+      float2 col[L1];
+#pragma unroll
+      for (int q = 0; q < L1; ++q)
+        col[q] = row_of<CL>(sm, q / ROWS)[(2 * (q % ROWS)) * kRowPitch + out_off + pad16(n2)];
+      dft<L1, +1>(col);
+      if (c + NT >= COLS) cluster_arrive<CL>();  // same iteration for every thread
+#pragma unroll
+      for (int n1 = 0; n1 < L1; ++n1) {
+        const int n = n2 + kRowN * n1;
+        if (n < I.n_out) __stcs(I.dst + n, col[n1]);
+      }
+    }
+    cluster_wait<CL>();                        // peers may still read our rows
+  }
+}
+
+template <int LOG2L1, int OP>
+cudaError_t launch_one(const FusedArgs& a, cudaStream_t s) {
+  constexpr int L1 = 1 << LOG2L1;
+  constexpr int ROWS = L1 >= kRowsPerCta ? kRowsPerCta : 1;
+  constexpr int CL = L1 / ROWS;
+  constexpr int NT = ROWS * kRowThreads;
+  const size_t smem = sizeof(float2) * ROWS * 2 * kRowPitch;
+  auto k = fused_kernel<LOG2L1, OP>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (CL > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n_items * CL));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
+
+template <int OP>
+cudaError_t launch_op(const FusedArgs& a, cudaStream_t s) {
+  switch (a.log2L) {
+    case 12: return launch_one<0, OP>(a, s);
+    case 13: return launch_one<1, OP>(a, s);
+    case 14: return launch_one<2, OP>(a, s);
+    case 15: return launch_one<3, OP>(a, s);
+    case 16: return launch_one<4, OP>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s) {
+  if (a.n_items <= 0) return cudaSuccess;
+  switch (op) {
+    case FUSED_APPLY: return launch_op<FUSED_APPLY>(a, s);
+    case FUSED_FULL: return launch_op<FUSED_FULL>(a, s);
+    case FUSED_SPEC: return launch_op<FUSED_SPEC>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dc

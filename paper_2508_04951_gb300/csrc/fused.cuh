@@ -1,0 +1,37 @@
+// Cluster-fused FFT correction for 4096 <= L <= 65536 (Sec. II-B, Eq. 16).
+//
+// L = L1 x 4096 with L1 = L / 4096 <= 16 rows of 4096 points.  One thread
+// block cluster owns one transform: each CTA holds two rows (one when L1 = 1)
+// in shared memory, 256 threads per row run the three radix-16 Stockham
+// stages of a row with the data in registers, and the column DFTs of length
+// L1 read the other CTAs' rows through distributed shared memory.  The
+// four-step intermediate never leaves the SMs, so a transform reads its input
+// once and writes its output once.
+//
+//   FUSED_APPLY : rows of a stored spectrum (bin k1 + L1 k2 at k1*4096 + k2)
+//                 times a phase table in the same layout (already scaled by
+//                 1/L) -> inverse rows -> W_L^(-n2 k1) -> inverse columns -> out
+//   FUSED_FULL  : y (zero-padded) -> forward columns (DSMEM scatter) ->
+//                 forward rows -> exp(-i phi_k) / L -> inverse rows ->
+//                 inverse columns -> out (truncated to n_out)
+//   FUSED_SPEC  : y -> forward columns -> forward rows -> spectrum rows
+#pragma once
+
+#include "fft.cuh"
+
+namespace dc {
+
+enum FusedOp : int { FUSED_APPLY = 0, FUSED_FULL = 1, FUSED_SPEC = 2 };
+
+struct FusedArgs {
+  const FftItem* items;   // one per transform (cluster)
+  int n_items;
+  int log2L;              // 12..16
+  const float2* tw;
+  int* err;               // device error flag (bounded waits)
+};
+
+// Launch; returns cudaErrorInvalidValue for L outside [4096, 65536].
+cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s);
+
+}  // namespace dc

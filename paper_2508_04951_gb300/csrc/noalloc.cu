@@ -3,8 +3,8 @@
 //
 // Everything this entry point touches on the device, apart from the caller's
 // input and output, lives in file-scope __device__ arrays of fixed size: the
-// four-step scratch (kNoAllocMax samples, 2 MiB), the twiddle tables and the
-// launch descriptors.  Each GPU that loads the library holds one copy of
+// four-step scratch (kNoAllocMax samples, 2 MiB), the twiddle tables (80 KiB)
+// and the launch descriptors.  Each GPU that loads the library holds one copy of
 // them until the process exits; nothing is allocated or freed per call.
 //
 // Host code cannot use these arrays' names as device addresses (in host code
@@ -18,6 +18,7 @@
 #include "../../include/dc.h"
 #include "fft.cuh"
 #include "phase.cuh"
+#include "twiddle_host.h"
 
 namespace {
 
@@ -56,16 +57,7 @@ dc_status prepare(int device, DeviceSlots** out) {
     if (cudaGetSymbolAddress(&p, g_items) != cudaSuccess) return DC_ECUDA;
     d.items = static_cast<dc::FftItem*>(p);
     static float2 tw[dc::kTwSize];
-    for (int t = 0; t < 4096; ++t) {
-      const double a = -2.0 * kPi * t / 4096.0;
-      tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    for (int j = 0; j < 1024; ++j) {
-      const double a = -2.0 * kPi * j / (double)(1 << 20);
-      tw[dc::kTwLo + j] = make_float2((float)std::cos(a), (float)std::sin(a));
-      const double b = -2.0 * kPi * j / 1024.0;
-      tw[dc::kTwHi + j] = make_float2((float)std::cos(b), (float)std::sin(b));
-    }
+    dc::fill_twiddles(tw);
     if (cudaMemcpy(d.twiddle, tw, sizeof tw, cudaMemcpyHostToDevice) != cudaSuccess)
       return DC_ECUDA;
     d.ready = true;

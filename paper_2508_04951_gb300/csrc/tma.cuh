@@ -1,0 +1,58 @@
+// Bulk asynchronous copies global -> shared (cp.async.bulk, the Blackwell TMA
+// engine's unswizzled 1-D form) completed through an mbarrier, with bounded
+// waits: a wait that runs out sets the caller's error flag instead of hanging.
+#pragma once
+
+#include "common.cuh"
+
+namespace dc {
+
+constexpr int kMbarPollLimit = 1 << 22;
+
+DC_DEV uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Thread 0 only, then a CTA barrier before use.
+DC_DEV void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+DC_DEV void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// dst, src 16-byte aligned; bytes a multiple of 16.
+DC_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+DC_DEV bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for phase `parity` with a poll limit; on timeout raise *err = 1 and
+// keep polling once more (bounded) for the copy still in flight.
+DC_DEV bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, int* err) {
+  for (int i = 0; i < kMbarPollLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, 1);
+  for (int i = 0; i < kMbarPollLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return false;
+  return false;
+}
+
+}  // namespace dc
