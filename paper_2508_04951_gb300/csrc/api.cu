@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/dc.h"
+#include "exact_tc.cuh"
 #include "fft.cuh"
 #include "fused.cuh"
 #include "phase.cuh"
@@ -75,10 +76,11 @@ dc_status cuda_fail(dc_ctx* c, cudaError_t e, const char* what) {
 // Kernel phases, named in dc_profile_read().
 enum Ph { PH_RS_TILED, PH_RS_DIRECT, PH_EXACT, PH_ROW_FULL, PH_COL_F1, PH_ROW_MID, PH_COL_B,
           PH_ROW_SPEC, PH_ROW_APPLY, PH_PHASE_TABLE, PH_FUSED_FULL, PH_FUSED_SPEC, PH_FUSED_APPLY,
-          PH_COUNT };
+          PH_EXACT_TC, PH_COUNT };
 const char* kPhaseName[PH_COUNT] = {"resample_tiled", "resample_direct", "exact_fp32", "row_full",
                                     "col_f1", "row_mid", "col_b", "row_spec", "row_apply",
-                                    "phase_table", "fused_full", "fused_spec", "fused_apply"};
+                                    "phase_table", "fused_full", "fused_spec", "fused_apply",
+                                    "exact_tc"};
 // Transform lengths handled by the cluster-fused kernels.
 bool fused_L(int log2L) { return log2L >= 12 && log2L <= 16; }
 
@@ -868,10 +870,32 @@ extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long 
   for (int i = 0; i < n_alpha; ++i)
     if ((st = check_pulse(c, n, n_out, 1.0, 0.0, v_r[i], 0.0))) return st;
   if (stride < 0) return fail(c, DC_EINVAL, "negative alpha stride");
-  if (mode != DC_EXACT_FP32)
-    return fail(c, DC_EINVAL, "mode %d not available in this build", mode);
+  if (mode != DC_EXACT_FP32 && mode != DC_EXACT_BF16X3 && mode != DC_EXACT_FP16X3)
+    return fail(c, DC_EINVAL, "unknown exact mode %d", mode);
   cudaSetDevice(c->device);
   cudaStream_t s = S(stream);
+  if (mode != DC_EXACT_FP32) {
+    // Tensor-core path: pulses of all alphas contiguous, or shared (stride 0).
+    if (stride != 0 && stride != (long long)n_pulses * n)
+      return fail(c, DC_EINVAL, "tensor-core exact mode needs x_alpha_stride 0 or n_pulses*n");
+    const long long rows_c = stride ? (long long)n_pulses * n_alpha : n_pulses;
+    Arena ar;
+    const size_t plane = exact_tc_plane_bytes(2 * rows_c, (int)n);
+    const size_t hi_at = ar.take(plane), lo_at = ar.take(plane);
+    if ((st = ensure_ws(c, ar.off))) return st;
+    if ((st = ensure_items(c, items_bytes_for(n_alpha)))) return st;
+    std::vector<float> dl(2 * (size_t)n_alpha);
+    for (int i = 0; i < n_alpha; ++i) split(alpha_minus_one(v_r[i]), dl[2 * i], dl[2 * i + 1]);
+    const float* ddl = nullptr;
+    if ((st = upload(c, dl, 0, s, &ddl))) return st;
+    ExTcArgs a{(int)n, (int)n_out, n_pulses, stride ? 2 * n_pulses : 0,
+               reinterpret_cast<float2*>(y), ddl, c->err};
+    Phase ph(c, PH_EXACT_TC, s, (long long)n_alpha * n_pulses * n_out);
+    cudaError_t e = launch_exact_tc(mode == DC_EXACT_FP16X3, reinterpret_cast<const float2*>(x), rows_c,
+                                    (int)n, c->ws + hi_at, c->ws + lo_at, a, n_alpha, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core exact launch");
+    return DC_OK;
+  }
   if ((st = ensure_items(c, items_bytes_for(n_alpha)))) return st;
   std::vector<ExItem> ex(n_alpha);
   for (int i = 0; i < n_alpha; ++i) {

@@ -1,0 +1,406 @@
+// Exact-sinc resampling as a tensor-core contraction (Eq. 17, Table I row 1):
+//
+//   Y_a[p][n] = sum_m X[p][m] S_a[n][m],   S_a[n][m] = sinc(a n - m),
+//
+// for many pulses p sharing one range rate a.  Treating the re/im parts of the
+// pulses as 2P real columns this is the GEMM  C[n][c] = sum_m S[n][m] X^T[m][c].
+// It runs on the 5th-generation tensor cores (tcgen05.mma, kind::f16) with
+// split operands: every FP32 value v is written as hi + lo with hi = rn(v) in
+// bf16 (or fp16) and lo = rn(v - hi); the product keeps the three significant
+// terms  S_hi X_hi + S_hi X_lo + S_lo X_hi  (dropping S_lo X_lo, ~2^-16 of the
+// result for bf16) with FP32 accumulation in tensor memory.  For fp16 the lo
+// parts are scaled by 2^11 (they would underflow fp16's range) and summed in a
+// second accumulator, C = acc1 + 2^-11 acc2.
+//
+// One CTA computes a 128 x 256 tile of C (128 output samples x 128 pulses):
+//   warp 0     TMA: X_hi / X_lo tiles (256 columns x 64 samples, 128B swizzle)
+//   warp 1     TMEM allocation; one thread issues the MMAs and commits
+//   warps 2-9  generate the S tile (128 x 64) in the same swizzled K-major
+//              layout, hi and lo, from the Cauchy form
+//              S[n][m] = (-1)^(m + m_n) sin(pi e_n) / (pi ((m_n - m) + e_n)),
+//              a n = m_n + e_n -- one division per element, no table
+//   warps 2-5  epilogue: TMEM -> registers (tcgen05.ld) -> complex64 outputs
+// Two pipeline stages of 96 KiB (S hi/lo 2 x 16 KiB, X hi/lo 2 x 32 KiB),
+// mbarriers between producers and the MMA thread, every wait bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "exact_tc.cuh"
+#include "tma.cuh"
+
+namespace dc {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int kStages = 2;
+constexpr int kABytes = BM * BK * 2;                 // 16 KiB per plane
+constexpr int kBBytes = BN * BK * 2;                 // 32 KiB per plane
+constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // + alignment slack
+constexpr int kThreads = 320;
+constexpr float kInvPi = 0.318309886183790672f;
+
+DC_DEV void bar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+DC_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+DC_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+DC_DEV void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128 B,
+// 8-row groups 1024 B apart (stride byte offset), descriptor version 1.
+DC_DEV uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) |
+         ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+
+// Instruction descriptor, kind::f16: D f32, A/B bf16 (or f16), both K-major,
+// N = 256, M = 128.
+template <bool FP16> __host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | ((FP16 ? 0u : 1u) << 7) | ((FP16 ? 0u : 1u) << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+DC_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+DC_DEV void mma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+DC_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+DC_DEV void tmem_ld16(uint32_t taddr, float (&f)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(r[i]);
+}
+
+// Split 8 floats into 8 hi and 8 lo 16-bit values (one 16-byte chunk each).
+template <bool FP16> DC_DEV void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if constexpr (FP16) {
+      const __half2 a = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+      const __half2 b = __floats2half2_rn((v[2 * i] - __low2float(a)) * 2048.f,
+                                          (v[2 * i + 1] - __high2float(a)) * 2048.f);
+      h[i] = *reinterpret_cast<const uint32_t*>(&a);
+      l[i] = *reinterpret_cast<const uint32_t*>(&b);
+    } else {
+      const __nv_bfloat162 a = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i] - __low2float(a),
+                                                     v[2 * i + 1] - __high2float(a));
+      h[i] = *reinterpret_cast<const uint32_t*>(&a);
+      l[i] = *reinterpret_cast<const uint32_t*>(&b);
+    }
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// a n = m_n + e_n with a - 1 a double-float (same arithmetic as the FP32 path).
+DC_DEV void position(float dl_hi, float dl_lo, int n, int& m, float& e) {
+  const float fi = (float)n;
+  df p = two_prod(dl_hi, fi);
+  const float lo = fmaf(dl_lo, fi, p.lo);
+  float f = floorf(p.hi);
+  float r = __fadd_rn(__fsub_rn(p.hi, f), lo);
+  if (r < 0.f) {
+    r = __fadd_rn(r, 1.f);
+    f -= 1.f;
+    if (r >= 1.f) { r = 0.f; f += 1.f; }
+  } else if (r >= 1.f) {
+    r = __fsub_rn(r, 1.f);
+    f += 1.f;
+  }
+  m = n + (int)f;
+  e = r;
+}
+
+template <bool FP16>
+__global__ void __launch_bounds__(kThreads, 1)
+    exact_tc_kernel(const __grid_constant__ CUtensorMap map_hi,
+                    const __grid_constant__ CUtensorMap map_lo, ExTcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], acc_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float s_sig[BM], s_e[BM];
+  __shared__ int s_m[BM];
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BM;
+  const int c0 = blockIdx.y * BN;
+  const int alpha = blockIdx.z;
+  const int nk = (a.n_in + BK - 1) / BK;
+  constexpr uint32_t kCols = FP16 ? 512 : 256;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1 + 256);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_base)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (warp >= 2 && threadIdx.x - 64 < BM) {
+    const int nl = threadIdx.x - 64;
+    int m;
+    float e;
+    position(a.dl[2 * alpha], a.dl[2 * alpha + 1], n0 + nl, m, e);
+    const float s = sinpif(e) * kInvPi;
+    s_m[nl] = m;
+    s_e[nl] = e;
+    s_sig[nl] = (m & 1) ? -s : s;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA
+    if (lane == 0) {
+      const int row0 = alpha * a.rows_per_alpha + c0;
+      for (int kc = 0; kc < nk && ok; ++kc) {
+        const int s = kc % kStages;
+        const uint32_t ph = (kc / kStages) & 1;
+        if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, a.err)) { ok = false; break; }
+        uint8_t* st = smem + s * kStageBytes;
+        mbar_expect_tx(&full_bar[s], 2 * kBBytes);
+        tma_load_2d(st + 2 * kABytes, &map_hi, kc * BK, row0, &full_bar[s]);
+        tma_load_2d(st + 2 * kABytes + kBBytes, &map_lo, kc * BK, row0, &full_bar[s]);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc<FP16>();
+      for (int kc = 0; kc < nk && ok; ++kc) {
+        const int s = kc % kStages;
+        const uint32_t ph = (kc / kStages) & 1;
+        if (!mbar_wait_bounded(&full_bar[s], ph, a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t st = smem_addr(smem + s * kStageBytes);
+        const uint32_t a_hi = st, a_lo = st + kABytes, b_hi = st + 2 * kABytes,
+                       b_lo = st + 2 * kABytes + kBBytes;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t off = kk * 32;     // 16 bf16 of K = 32 bytes inside the swizzle atom
+          const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+          if constexpr (FP16) {
+            mma_f16(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc);
+            mma_f16(tmem + 256, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, acc);
+            mma_f16(tmem + 256, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+          } else {
+            mma_f16(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc);
+            mma_f16(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+            mma_f16(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+          }
+        }
+        mma_commit(&empty_bar[s]);
+      }
+      mma_commit(&acc_bar);
+    }
+  } else {
+    // ------------------------------------------------- S tile producers
+    const int p = threadIdx.x - 64;            // 0..255
+    const int nl = p & (BM - 1), khalf = p >> 7;
+    const int mn = s_m[nl];
+    const float en = s_e[nl], sg = s_sig[nl];
+    for (int kc = 0; kc < nk && ok; ++kc) {
+      const int s = kc % kStages;
+      const uint32_t ph = (kc / kStages) & 1;
+      if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, a.err)) { ok = false; break; }
+      uint8_t* st = smem + s * kStageBytes;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k8 = khalf * 4 + q;         // 16-byte chunk of the 128-byte row
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int m = kc * BK + k8 * 8 + i;
+          float val = 0.f;
+          if (m < a.n_in) {
+            if (en == 0.f) val = (m == mn) ? 1.f : 0.f;
+            else val = __fdividef((i & 1) ? -sg : sg, (float)(mn - m) + en);
+          }
+          v[i] = val;
+        }
+        // (-1)^m: m = kc*64 + k8*8 + i has the parity of i
+        uint4 hi, lo;
+        split8<FP16>(v, hi, lo);
+        const int off = nl * 128 + ((k8 ^ (nl & 7)) << 4);
+        *reinterpret_cast<uint4*>(st + off) = hi;
+        *reinterpret_cast<uint4*>(st + kABytes + off) = lo;
+      }
+      async_proxy_fence();
+      bar_arrive(&full_bar[s]);
+    }
+    // ----------------------------------------------------------- epilogue
+    if (warp < 6) {
+      const int q = warp & 3;                   // TMEM lanes 32q .. 32q+31
+      const bool ready = mbar_wait_bounded(&acc_bar, 0, a.err);
+      tc_fence_after();
+      const int n = n0 + 32 * q + lane;
+      if (ready) {
+        for (int cc = 0; cc < BN / 16; ++cc) {
+          float f[16];
+          const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + cc * 16;
+          tmem_ld16(taddr, f);
+          if constexpr (FP16) {
+            float g[16];
+            tmem_ld16(taddr + 256, g);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) f[i] = fmaf(g[i], 1.0f / 2048.f, f[i]);
+          }
+          if (n < a.n_out) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int pulse = (c0 + cc * 16) / 2 + i;
+              if (pulse < a.n_pulses)
+                a.y[((size_t)alpha * a.n_pulses + pulse) * a.n_out + n] = make_float2(f[2 * i], f[2 * i + 1]);
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
+}
+
+// X (complex64, pulses of n samples) -> hi / lo 16-bit planes, row 2p = re,
+// row 2p + 1 = im, samples contiguous with row stride `ld` (lo scaled by 2^11
+// for fp16).
+template <bool FP16>
+__global__ void split_planes_kernel(const float2* __restrict__ x, int n, long long rows_c, int ld,
+                                    uint16_t* hi, uint16_t* lo) {
+  const long long total = rows_c * n;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long pr = g / n;
+    const int m = (int)(g - pr * n);
+    const float2 v = x[g];
+    const float vv[2] = {v.x, v.y};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      uint16_t h, l;
+      if constexpr (FP16) {
+        const __half a = __float2half_rn(vv[c]);
+        const __half b = __float2half_rn((vv[c] - __half2float(a)) * 2048.f);
+        h = __half_as_ushort(a);
+        l = __half_as_ushort(b);
+      } else {
+        const __nv_bfloat16 a = __float2bfloat16_rn(vv[c]);
+        const __nv_bfloat16 b = __float2bfloat16_rn(vv[c] - __bfloat162float(a));
+        h = __bfloat16_as_ushort(a);
+        l = __bfloat16_as_ushort(b);
+      }
+      const long long o = (2 * pr + c) * (long long)ld + m;
+      hi[o] = h;
+      lo[o] = l;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* base, bool fp16, long long rows, int n, int ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {BK, BN};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t exact_tc_plane_bytes(long long rows, int n) {
+  const long long ld = (n + 7) / 8 * 8;
+  return (size_t)rows * ld * 2;
+}
+
+cudaError_t launch_exact_tc(bool fp16, const float2* x, long long x_rows_c, int n, void* hi, void* lo,
+                            const ExTcArgs& args, int n_alpha, cudaStream_t s) {
+  const int ld = (n + 7) / 8 * 8;
+  const long long total = x_rows_c * n;
+  const int grid_c = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+  if (fp16)
+    split_planes_kernel<true><<<grid_c, 256, 0, s>>>(x, n, x_rows_c, ld, (uint16_t*)hi, (uint16_t*)lo);
+  else
+    split_planes_kernel<false><<<grid_c, 256, 0, s>>>(x, n, x_rows_c, ld, (uint16_t*)hi, (uint16_t*)lo);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mh, ml;
+  if (!make_map(&mh, hi, fp16, 2 * x_rows_c, n, ld) || !make_map(&ml, lo, fp16, 2 * x_rows_c, n, ld))
+    return cudaErrorInvalidValue;
+  dim3 grid((args.n_out + BM - 1) / BM, (2 * args.n_pulses + BN - 1) / BN, n_alpha);
+  if (fp16) {
+    auto k = exact_tc_kernel<true>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
+      return e;
+    k<<<grid, kThreads, kSmemBytes, s>>>(mh, ml, args);
+  } else {
+    auto k = exact_tc_kernel<false>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
+      return e;
+    k<<<grid, kThreads, kSmemBytes, s>>>(mh, ml, args);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dc
