@@ -12,16 +12,17 @@
 // parts are scaled by 2^11 (they would underflow fp16's range) and summed in a
 // second accumulator, C = acc1 + 2^-11 acc2.
 //
-// One CTA computes a 128 x 256 tile of C (128 output samples x 128 pulses):
-//   warp 0     TMA: X_hi / X_lo tiles (256 columns x 64 samples, 128B swizzle)
-//   warp 1     TMEM allocation; one thread issues the MMAs and commits
-//   warps 2-9  generate the S tile (128 x 64) in the same swizzled K-major
+// One CTA computes a 256 x 256 tile of C for bf16 (two 128-row MMA halves
+// sharing each X tile, halving the X traffic per flop) or 128 x 256 for fp16:
+//   warp 0     TMA: X_hi / X_lo tiles (256 columns x 32 samples, 64B swizzle)
+//   warp 1     TMEM allocation (512 columns); one thread issues the MMAs
+//   warps 2-9  generate the S tile (rows x 32) in the same swizzled K-major
 //              layout, hi and lo, from the Cauchy form
 //              S[n][m] = (-1)^(m + m_n) sin(pi e_n) / (pi ((m_n - m) + e_n)),
 //              a n = m_n + e_n -- one division per element, no table
-//   warps 2-5  epilogue: TMEM -> registers (tcgen05.ld) -> complex64 outputs
-// Two pipeline stages of 96 KiB (S hi/lo 2 x 16 KiB, X hi/lo 2 x 32 KiB),
-// mbarriers between producers and the MMA thread, every wait bounded.
+//   epilogue   TMEM -> registers (tcgen05.ld) -> complex64 outputs
+// Three (bf16) or four (fp16) pipeline stages of 64 / 48 KiB, mbarriers
+// between the producers and the MMA thread, every wait bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -36,13 +37,23 @@ namespace dc {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
-constexpr int kStages = 2;
-constexpr int kABytes = BM * BK * 2;                 // 16 KiB per plane
-constexpr int kBBytes = BN * BK * 2;                 // 32 KiB per plane
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // + alignment slack
+constexpr int BN = 256, BK = 32;                     // N columns, K per stage
+constexpr int kHalfRows = 128;                       // rows per MMA (M = 128)
+constexpr int kAPlane = kHalfRows * BK * 2;          // 8 KiB: one 128-row A plane
+constexpr int kBPlane = BN * BK * 2;                 // 16 KiB: one B plane
 constexpr int kThreads = 320;
+
+// bf16x3: two 128-row halves share every X tile (one accumulator each);
+// fp16x3: one half with two accumulators (hi*hi and the 2^11-scaled cross
+// terms).  Either way the 512 TMEM columns hold exactly the accumulators.
+template <bool FP16> struct Cfg {
+  static constexpr int MH = FP16 ? 1 : 2;            // 128-row halves per CTA
+  static constexpr int BM = MH * kHalfRows;
+  static constexpr int STAGES = FP16 ? 4 : 3;
+  static constexpr int A_BYTES = 2 * MH * kAPlane;   // hi + lo planes of all halves
+  static constexpr int STAGE = A_BYTES + 2 * kBPlane;
+  static constexpr int SMEM = STAGES * STAGE + 1024; // + alignment slack
+};
 constexpr float kInvPi = 0.318309886183790672f;
 
 DC_DEV void bar_arrive(unsigned long long* bar) {
@@ -52,18 +63,19 @@ DC_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;
 DC_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 DC_DEV void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128 B,
-// 8-row groups 1024 B apart (stride byte offset), descriptor version 1.
-DC_DEV uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 64 B =
+// 32 16-bit elements, the 16-byte chunk index XOR-ed with (row >> 1) & 3),
+// 8-row groups 512 B apart (stride byte offset), descriptor version 1.
+DC_DEV uint64_t sw64_desc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) |
-         ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+         ((uint64_t)(512u >> 4) << 32) | ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
 }
 
 // Instruction descriptor, kind::f16: D f32, A/B bf16 (or f16), both K-major,
 // N = 256, M = 128.
 template <bool FP16> __host__ __device__ constexpr uint32_t instr_desc() {
   return (1u << 4) | ((FP16 ? 0u : 1u) << 7) | ((FP16 ? 0u : 1u) << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(kHalfRows >> 4) << 24);
 }
 
 DC_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -147,24 +159,25 @@ template <bool FP16>
 __global__ void __launch_bounds__(kThreads, 1)
     exact_tc_kernel(const __grid_constant__ CUtensorMap map_hi,
                     const __grid_constant__ CUtensorMap map_lo, ExTcArgs a) {
+  using C = Cfg<FP16>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], acc_bar;
+  __shared__ __align__(8) unsigned long long full_bar[C::STAGES], empty_bar[C::STAGES], acc_bar;
   __shared__ uint32_t tmem_base;
-  __shared__ float s_sig[BM], s_e[BM];
-  __shared__ int s_m[BM];
+  __shared__ float s_sig[C::BM], s_e[C::BM];
+  __shared__ int s_m[C::BM];
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BM;
+  const int n0 = blockIdx.x * C::BM;
   const int c0 = blockIdx.y * BN;
   const int alpha = blockIdx.z;
   const int nk = (a.n_in + BK - 1) / BK;
-  constexpr uint32_t kCols = FP16 ? 512 : 256;
+  constexpr uint32_t kCols = 512;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full_bar[s], 1 + 256);
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full_bar[s], 1 + 8);   // TMA arrival + one per producer warp
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&acc_bar, 1);
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (warp >= 2 && threadIdx.x - 64 < BM) {
+  if (warp >= 2 && threadIdx.x - 64 < C::BM) {
     const int nl = threadIdx.x - 64;
     int m;
     float e;
@@ -196,13 +209,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const int row0 = alpha * a.rows_per_alpha + c0;
       for (int kc = 0; kc < nk && ok; ++kc) {
-        const int s = kc % kStages;
-        const uint32_t ph = (kc / kStages) & 1;
+        const int s = kc % C::STAGES;
+        const uint32_t ph = (kc / C::STAGES) & 1;
         if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, a.err)) { ok = false; break; }
-        uint8_t* st = smem + s * kStageBytes;
-        mbar_expect_tx(&full_bar[s], 2 * kBBytes);
-        tma_load_2d(st + 2 * kABytes, &map_hi, kc * BK, row0, &full_bar[s]);
-        tma_load_2d(st + 2 * kABytes + kBBytes, &map_lo, kc * BK, row0, &full_bar[s]);
+        uint8_t* st = smem + s * C::STAGE;
+        mbar_expect_tx(&full_bar[s], 2 * kBPlane);
+        tma_load_2d(st + C::A_BYTES, &map_hi, kc * BK, row0, &full_bar[s]);
+        tma_load_2d(st + C::A_BYTES + kBPlane, &map_lo, kc * BK, row0, &full_bar[s]);
       }
     }
   } else if (warp == 1) {
@@ -210,25 +223,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = instr_desc<FP16>();
       for (int kc = 0; kc < nk && ok; ++kc) {
-        const int s = kc % kStages;
-        const uint32_t ph = (kc / kStages) & 1;
+        const int s = kc % C::STAGES;
+        const uint32_t ph = (kc / C::STAGES) & 1;
         if (!mbar_wait_bounded(&full_bar[s], ph, a.err)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t st = smem_addr(smem + s * kStageBytes);
-        const uint32_t a_hi = st, a_lo = st + kABytes, b_hi = st + 2 * kABytes,
-                       b_lo = st + 2 * kABytes + kBBytes;
+        const uint32_t st = smem_addr(smem + s * C::STAGE);
+        const uint32_t b_hi = st + C::A_BYTES, b_lo = b_hi + kBPlane;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t off = kk * 32;     // 16 bf16 of K = 32 bytes inside the swizzle atom
+          const uint32_t off = kk * 32;     // 16 elements of K = 32 bytes inside the swizzle atom
           const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-          if constexpr (FP16) {
-            mma_f16(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc);
-            mma_f16(tmem + 256, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, acc);
-            mma_f16(tmem + 256, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
-          } else {
-            mma_f16(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc);
-            mma_f16(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-            mma_f16(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+#pragma unroll
+          for (int h = 0; h < C::MH; ++h) {
+            const uint32_t a_hi = st + h * kAPlane, a_lo = st + (C::MH + h) * kAPlane;
+            const uint32_t d = tmem + h * 256;
+            if constexpr (FP16) {
+              mma_f16(d, sw64_desc(a_hi + off), sw64_desc(b_hi + off), idesc, acc);
+              mma_f16(d + 256, sw64_desc(a_hi + off), sw64_desc(b_lo + off), idesc, acc);
+              mma_f16(d + 256, sw64_desc(a_lo + off), sw64_desc(b_hi + off), idesc, 1u);
+            } else {
+              mma_f16(d, sw64_desc(a_hi + off), sw64_desc(b_hi + off), idesc, acc);
+              mma_f16(d, sw64_desc(a_hi + off), sw64_desc(b_lo + off), idesc, 1u);
+              mma_f16(d, sw64_desc(a_lo + off), sw64_desc(b_hi + off), idesc, 1u);
+            }
           }
         }
         mma_commit(&empty_bar[s]);
@@ -237,49 +254,58 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------- S tile producers
+    // bf16: thread -> one of 256 rows, all 4 chunks of 8; fp16: one of 128
+    // rows, 2 of the 4 chunks.
+    constexpr int CHUNKS = FP16 ? 2 : 4;
     const int p = threadIdx.x - 64;            // 0..255
-    const int nl = p & (BM - 1), khalf = p >> 7;
+    const int nl = FP16 ? (p & 127) : p;
+    const int cbase = FP16 ? (p >> 7) * 2 : 0;
+    const int h = nl >> 7, r = nl & 127;       // half and row inside it
     const int mn = s_m[nl];
     const float en = s_e[nl], sg = s_sig[nl];
     for (int kc = 0; kc < nk && ok; ++kc) {
-      const int s = kc % kStages;
-      const uint32_t ph = (kc / kStages) & 1;
+      const int s = kc % C::STAGES;
+      const uint32_t ph = (kc / C::STAGES) & 1;
       if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, a.err)) { ok = false; break; }
-      uint8_t* st = smem + s * kStageBytes;
+      uint8_t* st = smem + s * C::STAGE;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k8 = khalf * 4 + q;         // 16-byte chunk of the 128-byte row
+      for (int q = 0; q < CHUNKS; ++q) {
+        const int k8 = cbase + q;              // 16-byte chunk of the 64-byte row
         float v[8];
+        const int m0 = kc * BK + k8 * 8;
+        const float d0 = (float)(mn - m0) + en;     // (m_n - m) + e_n at i = 0; exact steps of -1
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int m = kc * BK + k8 * 8 + i;
+          const int m = m0 + i;
           float val = 0.f;
           if (m < a.n_in) {
             if (en == 0.f) val = (m == mn) ? 1.f : 0.f;
-            else val = __fdividef((i & 1) ? -sg : sg, (float)(mn - m) + en);
+            else val = __fdividef((i & 1) ? -sg : sg, d0 - (float)i);
           }
           v[i] = val;
         }
-        // (-1)^m: m = kc*64 + k8*8 + i has the parity of i
+        // (-1)^m: m = kc*32 + k8*8 + i has the parity of i
         uint4 hi, lo;
         split8<FP16>(v, hi, lo);
-        const int off = nl * 128 + ((k8 ^ (nl & 7)) << 4);
-        *reinterpret_cast<uint4*>(st + off) = hi;
-        *reinterpret_cast<uint4*>(st + kABytes + off) = lo;
+        const int off = r * 64 + ((k8 ^ ((r >> 1) & 3)) << 4);
+        *reinterpret_cast<uint4*>(st + h * kAPlane + off) = hi;
+        *reinterpret_cast<uint4*>(st + (C::MH + h) * kAPlane + off) = lo;
       }
-      async_proxy_fence();
-      bar_arrive(&full_bar[s]);
+      async_proxy_fence();                     // our generic-proxy writes -> async proxy
+      __syncwarp();
+      if (lane == 0) bar_arrive(&full_bar[s]);
     }
     // ----------------------------------------------------------- epilogue
-    if (warp < 6) {
+    if (warp < 2 + 4 * C::MH) {
       const int q = warp & 3;                   // TMEM lanes 32q .. 32q+31
+      const int hh = (warp - 2) >> 2;           // accumulator half
       const bool ready = mbar_wait_bounded(&acc_bar, 0, a.err);
       tc_fence_after();
-      const int n = n0 + 32 * q + lane;
+      const int n = n0 + hh * kHalfRows + 32 * q + lane;
       if (ready) {
         for (int cc = 0; cc < BN / 16; ++cc) {
           float f[16];
-          const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + cc * 16;
+          const uint32_t taddr = tmem + hh * 256 + ((uint32_t)(32 * q) << 16) + cc * 16;
           tmem_ld16(taddr, f);
           if constexpr (FP16) {
             float g[16];
@@ -359,10 +385,10 @@ bool make_map(CUtensorMap* m, void* base, bool fp16, long long rows, int n, int 
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {BK, BN};
+  cuuint32_t box[2] = {BK, BN};      // 32 x 16-bit = 64 bytes inner: 64-byte swizzle
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
-                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -388,17 +414,18 @@ cudaError_t launch_exact_tc(bool fp16, const float2* x, long long x_rows_c, int 
   CUtensorMap mh, ml;
   if (!make_map(&mh, hi, fp16, 2 * x_rows_c, n, ld) || !make_map(&ml, lo, fp16, 2 * x_rows_c, n, ld))
     return cudaErrorInvalidValue;
-  dim3 grid((args.n_out + BM - 1) / BM, (2 * args.n_pulses + BN - 1) / BN, n_alpha);
   if (fp16) {
+    using Cf = Cfg<true>;
+    dim3 grid((args.n_out + Cf::BM - 1) / Cf::BM, (2 * args.n_pulses + BN - 1) / BN, n_alpha);
     auto k = exact_tc_kernel<true>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
-      return e;
-    k<<<grid, kThreads, kSmemBytes, s>>>(mh, ml, args);
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM))) return e;
+    k<<<grid, kThreads, Cf::SMEM, s>>>(mh, ml, args);
   } else {
+    using Cb = Cfg<false>;
+    dim3 grid((args.n_out + Cb::BM - 1) / Cb::BM, (2 * args.n_pulses + BN - 1) / BN, n_alpha);
     auto k = exact_tc_kernel<false>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
-      return e;
-    k<<<grid, kThreads, kSmemBytes, s>>>(mh, ml, args);
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cb::SMEM))) return e;
+    k<<<grid, kThreads, Cb::SMEM, s>>>(mh, ml, args);
   }
   return cudaGetLastError();
 }
