@@ -47,9 +47,11 @@ import synth  # noqa: E402
 METRIC = "corrected Msamples/s and p50/p99 pulse latency vs plain path at stated error"
 UNIT = "Msamples/s"
 ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
-# DRAM bytes per launch from an ncu capture of the kernel (None until taken for
-# the current kernel; summaries under profiles/).
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {}
+# DRAM bytes (read + write) per launch of the kernel at the full workload, from
+# one ncu capture (profiles/fused_apply_doppler_bank_32v.md: 232.6 MB for the
+# reduced 32-range-rate launch, scaled by the 8x units of the full launch).
+# Cleared whenever the kernel changes after the capture.
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 8 * 232.6e6}
 
 
 def load_peaks() -> tuple[float, str]:
@@ -337,6 +339,8 @@ def run_split(args) -> None:
     dcg.build.build()
     dcg.load()
     cfg = synth.SplitPrecisionBank()
+    if args.n_v:
+        cfg.n_alpha = args.n_v
     X, v = cfg.draw()
     X = X.astype(np.complex64)
     n, P, V = cfg.n, cfg.n_pulses, cfg.n_alpha
