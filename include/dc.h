@@ -210,6 +210,62 @@ DC_API dc_status resample_exact_batch(dc_ctx* ctx, const dc_c64* x_dev, long lon
                                long long x_alpha_stride, const double* v_r, int n_alpha,
                                dc_c64* y_dev, long long n_out, int mode, void* stream);
 
+/* Plans: a correct_batch or correct_bank call recorded once into a CUDA
+ * graph and replayed.  Creating a plan runs the call once on a private stream
+ * (the outputs are written), then records it with plan-owned scratch and item
+ * lists (uploaded once) and instantiates the graph.  The buffers and host
+ * lists the call was given must stay valid while the plan is used; every
+ * execution recomputes the outputs from the current contents of the input
+ * buffers.  dc_plan_execute enqueues one graph launch on `stream`; executions
+ * of one plan must not overlap on the GPU (they share its scratch).  This is
+ * how a batch runs as a single submission (Sec. II-B's bundling of FFT work). */
+typedef struct dc_plan dc_plan;
+DC_API dc_status dc_plan_batch(dc_ctx* ctx, const dc_c64* in_dev, dc_c64* out_dev,
+                               const dc_item* items, int n_items, const dc_opts* opts,
+                               dc_plan** plan);
+DC_API dc_status dc_plan_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n, const double* v_r,
+                              int n_v, const double* tec_tecu, int n_tec, dc_c64* out_dev,
+                              double fs, double fc, const dc_opts* opts, dc_plan** plan);
+DC_API dc_status dc_plan_execute(dc_plan* plan, void* stream);
+/* Kernel launches one execution replays (-1 for a null plan). */
+DC_API long long dc_plan_launches(const dc_plan* plan);
+DC_API dc_status dc_plan_destroy(dc_plan* plan);
+
+/* Serving loop with continuous batching (Sec. II-B's real-time use; the
+ * paper itself processes one pulse per launch).
+ *
+ * dc_serve_start creates a server on `device` whose scheduler thread keeps up
+ * to `slots` batches in flight.  Each slot owns a stream, a context and device
+ * buffers carved from `hbm_budget_bytes` (0 = 8 GiB): 48 bytes per sample of
+ * batch capacity, at most 32 Mi samples per slot; a slot must hold 2^20
+ * samples or the call fails with DC_EINVAL.  Requests are admitted into a free
+ * slot in arrival order while they fit its capacity (the HBM admission rule);
+ * a slot's batch runs H2D -> correct_batch -> D2H on its stream while the next
+ * slot fills with requests that arrived meanwhile.  Results do not depend on
+ * the batch a request rode in.
+ *
+ * dc_serve_submit queues one pulse (x_host: [n] samples, read when the request
+ * is admitted; y_host: [n] corrected samples, written before dc_serve_wait
+ * returns DC_OK; both must stay valid until then).  n <= 2^20.  Writes the
+ * request id.  dc_serve_wait blocks up to timeout_ms (< 0: forever) for a
+ * request (DC_ETIMEOUT if still running; the request stays valid), writes its
+ * latency from submission to completion, and forgets it.  dc_serve_cancel
+ * drops a request still queued (DC_EBUSY once admitted).  dc_serve_stats
+ * reports p50 / p99 latency, completed Msamples/s since the first submission,
+ * and the number of completed requests.  dc_serve_stop drains in-flight work
+ * and frees the server (requests not yet waited for are dropped). */
+typedef struct dc_server dc_server;
+DC_API dc_status dc_serve_start(int device, size_t hbm_budget_bytes, int slots, const dc_opts* opts,
+                                dc_server** server);
+DC_API dc_status dc_serve_submit(dc_server* server, const dc_c64* x_host, long long n, double fs,
+                                 double fc, double v_r, double tec_tecu, dc_c64* y_host,
+                                 long long* req_id);
+DC_API dc_status dc_serve_wait(dc_server* server, long long req_id, int timeout_ms, double* latency_s);
+DC_API dc_status dc_serve_cancel(dc_server* server, long long req_id);
+DC_API dc_status dc_serve_stats(dc_server* server, double* p50_s, double* p99_s,
+                                double* msamples_per_s, long long* completed);
+DC_API dc_status dc_serve_stop(dc_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,9 @@ __all__ = [
     "ITEM_DTYPE", "dc_opts_default", "dc_check", "dc_launch_count", "dc_profile_enable",
     "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc",
     "correct_batch", "correct_bank", "resample_exact_batch", "exported_symbols",
+    "Plan", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute", "dc_plan_launches",
+    "dc_plan_destroy", "Server", "dc_serve_start", "dc_serve_submit", "dc_serve_wait",
+    "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop",
 ]
 
 DC_WINDOWED, DC_EXACT_FP32, DC_EXACT_BF16X3, DC_EXACT_FP16X3 = 0, 1, 2, 3
@@ -90,6 +93,19 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "correct_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), vp]),
         "correct_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts), vp]),
         "resample_exact_batch": (i, [vp, vp, ll, i, ll, dp, i, vp, ll, i, vp]),
+        "dc_plan_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), ctypes.POINTER(vp)]),
+        "dc_plan_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts),
+                             ctypes.POINTER(vp)]),
+        "dc_plan_execute": (i, [vp, vp]),
+        "dc_plan_launches": (ll, [vp]),
+        "dc_plan_destroy": (i, [vp]),
+        "dc_serve_start": (i, [i, ctypes.c_size_t, i, ctypes.POINTER(DcOpts), ctypes.POINTER(vp)]),
+        "dc_serve_submit": (i, [vp, vp, ll, d, d, d, d, vp, ctypes.POINTER(ll)]),
+        "dc_serve_wait": (i, [vp, ll, i, ctypes.POINTER(d)]),
+        "dc_serve_cancel": (i, [vp, ll]),
+        "dc_serve_stats": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
+                               ctypes.POINTER(ll)]),
+        "dc_serve_stop": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -103,7 +119,9 @@ def exported_symbols() -> list[str]:
     """Names of the C entry points this binding binds (all declared in dc.h)."""
     return ["dc_opts_default", "dc_status_str", "dc_create", "dc_destroy", "dc_last_error",
             "dc_check", "dc_launch_count", "dc_profile_enable", "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc", "correct_batch", "correct_bank",
-            "resample_exact_batch"]
+            "resample_exact_batch", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute",
+            "dc_plan_launches", "dc_plan_destroy", "dc_serve_start", "dc_serve_submit",
+            "dc_serve_wait", "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop"]
 
 
 # ---------------------------------------------------------------- helpers
@@ -253,3 +271,153 @@ def resample_exact_batch(ctx: Context, x, n: int, n_pulses: int, v_r, y, *, n_ou
     ctx.check(ctx.lib.resample_exact_batch(ctx.handle, _ptr(x), int(n), int(n_pulses),
                                            int(x_alpha_stride), _dptr(v), len(v), _ptr(y),
                                            int(n_out), int(mode), _stream(stream)))
+
+
+# ------------------------------------------------------------------- plans
+
+class Plan:
+    """A correct_batch / correct_bank call recorded into a CUDA graph.  Keeps
+    references to the tensors and host lists it was built from."""
+
+    def __init__(self, ctx: Context, handle, keep):
+        self.ctx, self.handle, self._keep = ctx, handle, keep
+
+    def execute(self, stream=None) -> None:
+        dc_plan_execute(self, stream=stream)
+
+    @property
+    def launches(self) -> int:
+        return dc_plan_launches(self)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.dc_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dc_plan_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_WINDOWED) -> Plan:
+    it = np.ascontiguousarray(np.asarray(items, dtype=ITEM_DTYPE))
+    o = _opts(taps, beta, mode, 0)
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.dc_plan_batch(ctx.handle, _ptr(inp), _ptr(out), it.ctypes.data, len(it),
+                                    ctypes.byref(o), ctypes.byref(h)))
+    return Plan(ctx, h, (inp, out, it))
+
+
+def dc_plan_bank(ctx: Context, x, v_r, tec_tecu, out, fs: float, fc: float, *, taps=32, beta=8.0,
+                 n_out=0) -> Plan:
+    v = np.ascontiguousarray(np.asarray(v_r, dtype=np.float64))
+    t = np.ascontiguousarray(np.asarray(tec_tecu, dtype=np.float64))
+    o = _opts(taps, beta, DC_WINDOWED, n_out)
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.dc_plan_bank(ctx.handle, _ptr(x), x.numel(), _dptr(v), len(v), _dptr(t), len(t),
+                                   _ptr(out), fs, fc, ctypes.byref(o), ctypes.byref(h)))
+    return Plan(ctx, h, (x, out, v, t))
+
+
+def dc_plan_execute(plan: Plan, stream=None) -> None:
+    plan.ctx.check(plan.ctx.lib.dc_plan_execute(plan.handle, _stream(stream)))
+
+
+def dc_plan_launches(plan: Plan) -> int:
+    return int(plan.ctx.lib.dc_plan_launches(plan.handle))
+
+
+def dc_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """A dc_server: continuous-batching request loop on one device.  Host
+    buffers of submitted requests are kept referenced until waited for."""
+
+    def __init__(self, handle, lib):
+        self.handle, self.lib = handle, lib
+        self._keep = {}
+
+    def submit(self, x, y, fs, fc, v_r, tec_tecu) -> int:
+        return dc_serve_submit(self, x, y, fs, fc, v_r, tec_tecu)
+
+    def wait(self, req_id, timeout_ms=-1) -> float:
+        return dc_serve_wait(self, req_id, timeout_ms)
+
+    def stats(self) -> dict:
+        return dc_serve_stats(self)
+
+    def stop(self):
+        dc_serve_stop(self)
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+
+def _host_c64(a, name):
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex64 or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a contiguous complex64 numpy array")
+    return a.ctypes.data
+
+
+def dc_serve_start(device: int = 0, budget_bytes: int = 0, slots: int = 3, *, taps=32, beta=8.0,
+                   mode=DC_WINDOWED) -> Server:
+    lib = load()
+    o = _opts(taps, beta, mode, 0)
+    h = ctypes.c_void_p()
+    st = lib.dc_serve_start(int(device), int(budget_bytes), int(slots), ctypes.byref(o), ctypes.byref(h))
+    if st:
+        raise DcError(st, "dc_serve_start failed")
+    return Server(h, lib)
+
+
+def dc_serve_submit(srv: Server, x, y, fs, fc, v_r, tec_tecu) -> int:
+    rid = ctypes.c_longlong()
+    st = srv.lib.dc_serve_submit(srv.handle, _host_c64(x, "x"), x.size, float(fs), float(fc), float(v_r),
+                                 float(tec_tecu), _host_c64(y, "y"), ctypes.byref(rid))
+    if st:
+        raise DcError(st, "dc_serve_submit rejected the request")
+    srv._keep[rid.value] = (x, y)
+    return rid.value
+
+
+def dc_serve_wait(srv: Server, req_id: int, timeout_ms: int = -1) -> float:
+    lat = ctypes.c_double()
+    st = srv.lib.dc_serve_wait(srv.handle, int(req_id), int(timeout_ms), ctypes.byref(lat))
+    if st == 5:
+        raise DcError(st, f"request {req_id} still running")
+    srv._keep.pop(req_id, None)
+    if st:
+        raise DcError(st, f"request {req_id} failed")
+    return lat.value
+
+
+def dc_serve_cancel(srv: Server, req_id: int) -> None:
+    st = srv.lib.dc_serve_cancel(srv.handle, int(req_id))
+    if st:
+        raise DcError(st, f"request {req_id} could not be cancelled")
+
+
+def dc_serve_stats(srv: Server) -> dict:
+    p50, p99, msps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_longlong()
+    st = srv.lib.dc_serve_stats(srv.handle, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(msps),
+                                ctypes.byref(n))
+    if st:
+        raise DcError(st, "dc_serve_stats failed")
+    return {"p50_s": p50.value, "p99_s": p99.value, "msamples_per_s": msps.value, "completed": n.value}
+
+
+def dc_serve_stop(srv: Server) -> None:
+    if getattr(srv, "handle", None):
+        srv.lib.dc_serve_stop(srv.handle)
+        srv.handle = None
+        srv._keep.clear()

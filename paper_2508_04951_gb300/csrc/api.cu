@@ -46,6 +46,9 @@ struct dc_ctx {
   char* items = nullptr;      // device item arrays
   size_t items_bytes = 0;
   long long launches = 0;     // kernels launched by this context
+  // While a plan is being recorded: item uploads go to this host staging
+  // buffer (copied to the plan's device item buffer once the capture ends).
+  std::vector<char>* rec = nullptr;
   // per-phase CUDA-event timing (dc_profile_enable / dc_profile_read)
   bool profiling = false;
   struct Rec { int phase; cudaEvent_t a, b; long long samples; };
@@ -54,7 +57,7 @@ struct dc_ctx {
   double acc_ms[16] = {};
   long long acc_launches[16] = {};
   long long acc_samples[16] = {};
-  std::mutex mu;
+  std::recursive_mutex mu;
 };
 
 namespace {
@@ -106,7 +109,7 @@ struct Phase {
   Phase(dc_ctx* c_, int id_, cudaStream_t s_, long long samples_)
       : c(c_), id(id_), s(s_), samples(samples_) {
     ++c->launches;
-    if (c->profiling) {
+    if (c->profiling && !c->rec) {
       a = take_event(c);
       cudaEventRecord(a, s);
     }
@@ -152,6 +155,7 @@ PhaseParams phase_params(double fs, double fc, double tec_tecu, int log2L) {
 // block stays allocated until destroy, since queued work may still use it).
 dc_status ensure_ws(dc_ctx* c, size_t bytes) {
   if (bytes <= c->ws_bytes) return DC_OK;
+  if (c->rec) return fail(c, DC_ENOMEM, "plan scratch too small");
   if (c->budget && bytes > c->budget)
     return fail(c, DC_EBUSY, "scratch of %zu bytes exceeds the context budget of %zu", bytes,
                 c->budget);
@@ -171,6 +175,7 @@ dc_status ensure_ws(dc_ctx* c, size_t bytes) {
 
 dc_status ensure_items(dc_ctx* c, size_t bytes) {
   if (bytes <= c->items_bytes) return DC_OK;
+  if (c->rec) return fail(c, DC_ENOMEM, "plan item buffer too small");
   size_t want = std::max(bytes, (size_t)1 << 16);
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, want);
@@ -254,9 +259,14 @@ cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 // the pageable source may be reused as soon as this returns).
 template <class T>
 dc_status upload(dc_ctx* c, const std::vector<T>& v, size_t at, cudaStream_t s, const T** dev) {
-  cudaError_t e = cudaMemcpyAsync(c->items + at, v.data(), v.size() * sizeof(T),
-                                  cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "item upload");
+  const size_t bytes = v.size() * sizeof(T);
+  if (at + bytes > c->items_bytes) return fail(c, DC_ENOMEM, "item list overflow");
+  if (c->rec) {
+    memcpy(c->rec->data() + at, v.data(), bytes);
+  } else {
+    cudaError_t e = cudaMemcpyAsync(c->items + at, v.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "item upload");
+  }
   *dev = reinterpret_cast<const T*>(c->items + at);
   return DC_OK;
 }
@@ -458,7 +468,7 @@ long long dc_launch_count(const dc_ctx* c) { return c ? c->launches : -1; }
 
 dc_status dc_profile_enable(dc_ctx* c, int on) {
   if (!c) return DC_EINVAL;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   for (auto& r : c->pending) {
     cudaEventSynchronize(r.b);
     c->pool.push_back(r.a);
@@ -472,7 +482,7 @@ dc_status dc_profile_enable(dc_ctx* c, int on) {
 
 int dc_profile_read(dc_ctx* c, dc_phase_time* out, int max) {
   if (!c) return -1;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   for (auto& r : c->pending) {
     cudaEventSynchronize(r.b);
     float ms = 0.f;
@@ -501,7 +511,7 @@ int dc_profile_read(dc_ctx* c, dc_phase_time* out, int max) {
 
 dc_status dc_check(dc_ctx* c, void* stream) {
   if (!c) return DC_EINVAL;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   cudaError_t e = cudaStreamSynchronize(S(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
   int flag = 0;
@@ -518,7 +528,7 @@ dc_status dc_check(dc_ctx* c, void* stream) {
 dc_status doppler_resample(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, double fs,
                            double fc, double v_r, const dc_opts* opts, void* stream) {
   if (!c) return DC_EINVAL;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   dc_opts o;
   dc_opts_default(&o);
   if (opts) o = *opts;
@@ -557,7 +567,7 @@ dc_status doppler_resample(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, d
 dc_status iono_correct(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, double fs, double fc,
                        double tec, void* stream) {
   if (!c) return DC_EINVAL;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   dc_status st = check_pulse(c, n, n, fs, fc, 0.0, tec);
   if (st) return st;
   if (!x || !y) return fail(c, DC_EINVAL, "null buffer");
@@ -580,7 +590,7 @@ dc_status iono_correct(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, doubl
 dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item* items,
                         int n_items, const dc_opts* opts, void* stream) {
   if (!c) return DC_EINVAL;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   dc_opts o;
   dc_opts_default(&o);
   if (opts) o = *opts;
@@ -699,7 +709,7 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
                                   int n_v, const double* tec, int n_tec, dc_c64* out, double fs,
                                   double fc, const dc_opts* opts, void* stream) {
   if (!c) return DC_EINVAL;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   dc_opts o;
   dc_opts_default(&o);
   if (opts) o = *opts;
@@ -727,10 +737,9 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   const size_t s_at = ar.take((size_t)n_v * L * sizeof(float2));
   const size_t t_at =
       ar.take(fused_L(log2L) ? 0 : (size_t)std::max(chunk, four ? n_v : 0) * L * sizeof(float2));
-  const size_t ph_at = ar.take((size_t)n_tec * sizeof(PhaseParams));
   if ((st = ensure_ws(c, ar.off))) return st;
   const size_t n_pairs = (size_t)n_v * n_tec;
-  if ((st = ensure_items(c, items_bytes_for(n_pairs * 2 + n_v * 6)))) return st;
+  if ((st = ensure_items(c, items_bytes_for(n_pairs * 2 + n_v * 6 + n_tec)))) return st;
   char* ws = c->ws;
   float2* Yr = reinterpret_cast<float2*>(ws + y_at);
   float2* P = reinterpret_cast<float2*>(ws + p_at);
@@ -742,15 +751,14 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   // 1. phase table
   std::vector<PhaseParams> ph(n_tec);
   for (int t = 0; t < n_tec; ++t) ph[t] = phase_params(fs, fc, tec[t], log2L);
-  if ((e = cudaMemcpyAsync(ws + ph_at, ph.data(), n_tec * sizeof(PhaseParams),
-                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_fail(c, e, "phase upload");
+  const PhaseParams* dph = nullptr;
+  if ((st = upload(c, ph, item_at, s, &dph))) return st;
+  item_at += (n_tec * sizeof(PhaseParams) + 255) & ~(size_t)255;
   {
     const size_t total = L * n_tec;
     const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
-    Phase ph(c, PH_PHASE_TABLE, s, (long long)total);
-    phase_table_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const PhaseParams*>(ws + ph_at), n_tec,
-                                             log2L, fused_L(log2L) ? 1 : 0, P);
+    Phase phs(c, PH_PHASE_TABLE, s, (long long)total);
+    phase_table_kernel<<<grid, 256, 0, s>>>(dph, n_tec, log2L, fused_L(log2L) ? 1 : 0, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "phase table launch");
   }
   // 2. resample per v_r
@@ -862,7 +870,7 @@ extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long 
                                           long long stride, const double* v_r, int n_alpha,
                                           dc_c64* y, long long n_out, int mode, void* stream) {
   if (!c) return DC_EINVAL;
-  std::lock_guard<std::mutex> g(c->mu);
+  std::lock_guard<std::recursive_mutex> g(c->mu);
   if (!x || !y || !v_r || n_alpha < 1 || n_pulses < 1)
     return fail(c, DC_EINVAL, "bad exact-batch arguments");
   if (n_out == 0) n_out = n;
@@ -909,5 +917,135 @@ extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long 
   Phase ph(c, PH_EXACT, s, (long long)n_alpha * n_pulses * n_out);
   cudaError_t e = launch_exact_fp32(a, n_alpha, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "exact launch");
+  return DC_OK;
+}
+
+// ================================================================ plans
+// A plan is one of the calls above recorded once into a CUDA graph: the call
+// runs once on a private stream (sizing the context's scratch and warming
+// up), then again with the plan's own scratch and item buffers swapped in,
+// item uploads staged on the host and every kernel launch captured.  The
+// staged items are copied to the plan's device buffer and the graph is
+// instantiated; dc_plan_execute replays it with one cudaGraphLaunch.
+struct dc_plan {
+  dc_ctx* c = nullptr;
+  char* ws = nullptr;
+  char* items = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
+
+namespace {
+
+template <class F>
+dc_status make_plan(dc_ctx* c, F&& call, dc_plan** out) {
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  *out = nullptr;
+  cudaSetDevice(c->device);
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(c, e, "plan stream");
+  dc_status st = call(cs);
+  if (!st && (e = cudaStreamSynchronize(cs)) != cudaSuccess) st = cuda_fail(c, e, "plan warm-up");
+  dc_plan* p = nullptr;
+  if (!st) {
+    p = new dc_plan();
+    p->c = c;
+    if (cudaMalloc(&p->ws, std::max<size_t>(c->ws_bytes, 256)) != cudaSuccess ||
+        cudaMalloc(&p->items, c->items_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(c, DC_ENOMEM, "plan buffers");
+    }
+  }
+  if (!st) {
+    char* ws0 = c->ws;
+    char* it0 = c->items;
+    std::vector<char> staging(c->items_bytes, 0);
+    c->ws = p->ws;
+    c->items = p->items;
+    c->rec = &staging;
+    const long long l0 = c->launches;
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      st = cuda_fail(c, e, "begin capture");
+    } else {
+      dc_status st2 = call(cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (st2) st = st2;
+      else if (e != cudaSuccess) st = cuda_fail(c, e, "end capture");
+    }
+    c->rec = nullptr;
+    c->ws = ws0;
+    c->items = it0;
+    p->launches = c->launches - l0;
+    c->launches = l0;
+    if (!st && (e = cudaMemcpy(p->items, staging.data(), staging.size(), cudaMemcpyHostToDevice)) !=
+                   cudaSuccess)
+      st = cuda_fail(c, e, "plan item upload");
+    if (!st && (e = cudaGraphInstantiate(&p->exec, graph, 0)) != cudaSuccess)
+      st = cuda_fail(c, e, "graph instantiate");
+    if (graph) cudaGraphDestroy(graph);
+  }
+  cudaStreamDestroy(cs);
+  if (st) {
+    if (p) {
+      if (p->exec) cudaGraphExecDestroy(p->exec);
+      if (p->ws) cudaFree(p->ws);
+      if (p->items) cudaFree(p->items);
+      delete p;
+    }
+    return st;
+  }
+  *out = p;
+  return DC_OK;
+}
+
+}  // namespace
+
+extern "C" dc_status dc_plan_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item* items,
+                                   int n_items, const dc_opts* opts, dc_plan** plan) {
+  if (!c || !plan) return DC_EINVAL;
+  std::vector<dc_item> copy(items, items + (items ? n_items : 0));
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  return make_plan(
+      c, [&](cudaStream_t s) { return correct_batch(c, in, out, copy.data(), n_items, &o, s); }, plan);
+}
+
+extern "C" dc_status dc_plan_bank(dc_ctx* c, const dc_c64* x, long long n, const double* v_r, int n_v,
+                                  const double* tec, int n_tec, dc_c64* out, double fs, double fc,
+                                  const dc_opts* opts, dc_plan** plan) {
+  if (!c || !plan || !v_r || !tec || n_v < 1 || n_tec < 1) return DC_EINVAL;
+  std::vector<double> v(v_r, v_r + n_v), t(tec, tec + n_tec);
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  return make_plan(
+      c,
+      [&](cudaStream_t s) {
+        return correct_bank(c, x, n, v.data(), n_v, t.data(), n_tec, out, fs, fc, &o, s);
+      },
+      plan);
+}
+
+extern "C" dc_status dc_plan_execute(dc_plan* p, void* stream) {
+  if (!p || !p->exec) return DC_EINVAL;
+  cudaError_t e = cudaGraphLaunch(p->exec, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(p->c, e, "graph launch");
+  p->c->launches += p->launches;
+  return DC_OK;
+}
+
+extern "C" long long dc_plan_launches(const dc_plan* p) { return p ? p->launches : -1; }
+
+extern "C" dc_status dc_plan_destroy(dc_plan* p) {
+  if (!p) return DC_EINVAL;
+  cudaSetDevice(p->c->device);
+  cudaDeviceSynchronize();
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->ws) cudaFree(p->ws);
+  if (p->items) cudaFree(p->items);
+  delete p;
   return DC_OK;
 }

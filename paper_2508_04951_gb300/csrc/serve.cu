@@ -1,0 +1,325 @@
+// Serving loop with continuous batching (host C++; declared in include/dc.h).
+//
+// Requests (host pulses with their own fs, fc, v_r and TEC) are queued by
+// dc_serve_submit.  One scheduler thread owns `slots` batch slots, each with
+// its own stream, context (so scratch is never shared between batches in
+// flight), device in/out buffers and pinned staging, all sized from the HBM
+// budget at start.  Whenever a slot is free and requests wait, the scheduler
+// admits queued requests into it in arrival order while they fit its sample
+// capacity, copies their samples into pinned staging, and enqueues
+// H2D -> correct_batch -> D2H -> event on the slot's stream; it does not wait
+// for the GPU, so the next slot fills with requests that arrive meanwhile and
+// batches overlap on the device.  Completed slots (event query) hand results
+// back to the callers' buffers and record the latency from submission to
+// completion.  Each request's result does not depend on which batch it rode in
+// (correct_batch's per-item independence).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dc.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  long long id;
+  const dc_c64* x;
+  dc_c64* y;
+  long long n;
+  double fs, fc, v_r, tec;
+  Clock::time_point t_submit, t_done;
+  int state = 0;          // 0 queued, 1 in flight, 2 done, 3 failed, 4 cancelled
+  dc_status status = DC_OK;
+};
+
+struct Slot {
+  dc_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  dc_c64* in_dev = nullptr;
+  dc_c64* out_dev = nullptr;
+  dc_c64* in_host = nullptr;    // pinned
+  dc_c64* out_host = nullptr;   // pinned
+  long long cap = 0;            // samples
+  std::vector<Request*> reqs;
+  std::vector<long long> offs;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct dc_server {
+  int device = 0;
+  dc_opts opts{};
+  std::vector<Slot> slots;
+  long long cap = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::unordered_map<long long, Request*> reqs;
+  long long next_id = 1;
+  bool stop = false;
+  std::thread th;
+  // statistics
+  std::vector<double> latencies;
+  long long done_samples = 0, completed = 0, batches = 0;
+  Clock::time_point t_first{}, t_last{};
+  bool have_first = false;
+};
+
+namespace {
+
+// Hand a completed slot's results back (called with the lock held; drops it
+// while copying: the slot's requests are in flight, which waiters and cancel
+// leave alone).
+void finish_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
+  const cudaError_t e = cudaEventQuery(sl.done);
+  lk.unlock();
+  if (e == cudaSuccess)
+    for (size_t i = 0; i < sl.reqs.size(); ++i)
+      memcpy(sl.reqs[i]->y, sl.out_host + sl.offs[i], (size_t)sl.reqs[i]->n * sizeof(dc_c64));
+  const auto now = Clock::now();
+  lk.lock();
+  for (Request* r : sl.reqs) {
+    r->state = e == cudaSuccess ? 2 : 3;
+    r->status = e == cudaSuccess ? DC_OK : DC_ECUDA;
+    if (e == cudaSuccess) s->done_samples += r->n;
+    r->t_done = now;
+    s->latencies.push_back(std::chrono::duration<double>(now - r->t_submit).count());
+    ++s->completed;
+  }
+  s->t_last = now;
+  sl.reqs.clear();
+  sl.offs.clear();
+  sl.busy = false;
+  s->cv_done.notify_all();
+}
+
+// Admit queued requests into a free slot and enqueue its work (called with
+// the lock held; drops it while staging and enqueuing).
+bool launch_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
+  long long used = 0;
+  while (!s->queue.empty()) {
+    Request* r = s->queue.front();
+    const long long need = (r->n + 1) & ~1LL;   // keep 16-byte alignment of offsets
+    if (used + need > sl.cap) break;
+    s->queue.pop_front();
+    sl.reqs.push_back(r);
+    sl.offs.push_back(used);
+    used += need;
+    r->state = 1;
+  }
+  if (sl.reqs.empty()) return false;
+  sl.busy = true;
+  lk.unlock();
+  std::vector<dc_item> items(sl.reqs.size());
+  for (size_t i = 0; i < sl.reqs.size(); ++i) {
+    Request* r = sl.reqs[i];
+    memcpy(sl.in_host + sl.offs[i], r->x, (size_t)r->n * sizeof(dc_c64));
+    items[i] = dc_item{sl.offs[i], r->n, sl.offs[i], r->n, r->fs, r->fc, r->v_r, r->tec};
+  }
+  dc_status st = DC_OK;
+  if (cudaMemcpyAsync(sl.in_dev, sl.in_host, (size_t)used * sizeof(dc_c64), cudaMemcpyHostToDevice,
+                      sl.stream) != cudaSuccess)
+    st = DC_ECUDA;
+  if (!st) st = correct_batch(sl.ctx, sl.in_dev, sl.out_dev, items.data(), (int)items.size(), &s->opts,
+                              sl.stream);
+  if (!st && cudaMemcpyAsync(sl.out_host, sl.out_dev, (size_t)used * sizeof(dc_c64),
+                             cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+    st = DC_ECUDA;
+  if (!st && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = DC_ECUDA;
+  lk.lock();
+  if (st) {
+    const auto now = Clock::now();
+    for (Request* r : sl.reqs) {
+      r->state = 3;
+      r->status = st;
+      r->t_done = now;
+    }
+    sl.reqs.clear();
+    sl.offs.clear();
+    sl.busy = false;
+    s->cv_done.notify_all();
+    return false;
+  }
+  ++s->batches;
+  return true;
+}
+
+void scheduler(dc_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    bool progress = false;
+    for (Slot& sl : s->slots)
+      if (sl.busy && !sl.reqs.empty() && cudaEventQuery(sl.done) != cudaErrorNotReady) {
+        finish_slot(s, sl, lk);
+        progress = true;
+      }
+    for (Slot& sl : s->slots)
+      if (!sl.busy && !s->queue.empty()) progress |= launch_slot(s, sl, lk);
+    bool any_busy = false;
+    for (Slot& sl : s->slots) any_busy |= sl.busy;
+    if (s->stop && !any_busy) break;
+    if (!progress) {
+      // nothing to do right now: sleep until a submission, or poll the GPU
+      if (any_busy || s->stop)
+        s->cv_work.wait_for(lk, std::chrono::microseconds(50));
+      else
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" dc_status dc_serve_start(int device, size_t hbm_budget_bytes, int slots, const dc_opts* opts,
+                                    dc_server** out) {
+  if (!out || slots < 1 || slots > 16) return DC_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return DC_EINVAL;
+  dc_server* s = new dc_server();
+  s->device = device;
+  dc_opts_default(&s->opts);
+  if (opts) s->opts = *opts;
+  // Per slot: in + out buffers (16 B/sample) plus correct_batch scratch
+  // (resampled copy and, for L > 65536, a four-step buffer of up to 2x):
+  // budget 48 B per sample of capacity, at most kSlotMax samples per batch.
+  constexpr long long kSlotMax = 32LL << 20;
+  const size_t budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)8 << 30);
+  s->cap = std::min<long long>((long long)(budget / slots / 48), kSlotMax);
+  if (s->cap < (1LL << 20)) {
+    delete s;
+    return DC_EINVAL;            // each slot must hold the largest pulse (2^20 samples)
+  }
+  s->slots.resize(slots);
+  for (Slot& sl : s->slots) {
+    sl.cap = s->cap;
+    const size_t bytes = (size_t)sl.cap * sizeof(dc_c64);
+    if (dc_create(&sl.ctx, device, (size_t)sl.cap * 32) != DC_OK ||
+        cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&sl.in_dev, bytes) != cudaSuccess || cudaMalloc(&sl.out_dev, bytes) != cudaSuccess ||
+        cudaMallocHost(&sl.in_host, bytes) != cudaSuccess ||
+        cudaMallocHost(&sl.out_host, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      dc_serve_stop(s);
+      return DC_ENOMEM;
+    }
+  }
+  s->th = std::thread(scheduler, s);
+  *out = s;
+  return DC_OK;
+}
+
+extern "C" dc_status dc_serve_submit(dc_server* s, const dc_c64* x_host, long long n, double fs,
+                                     double fc, double v_r, double tec_tecu, dc_c64* y_host,
+                                     long long* req_id) {
+  if (!s || !x_host || !y_host || !req_id) return DC_EINVAL;
+  if (n < 1 || n > (1LL << 20) || n > s->cap) return DC_EINVAL;
+  if (!(fs > 0.0) || !(fc >= 0.0) || (fc != 0.0 && !(fc > fs / 2.0)) || !(v_r > -299792458.0) ||
+      !(v_r < 299792458.0) || !(tec_tecu == tec_tecu))
+    return DC_EINVAL;
+  Request* r = new Request{0, x_host, y_host, n, fs, fc, v_r, tec_tecu, Clock::now(), {}, 0, DC_OK};
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->stop) {
+      delete r;
+      return DC_ECANCELLED;
+    }
+    r->id = s->next_id++;
+    if (!s->have_first) {
+      s->t_first = r->t_submit;
+      s->have_first = true;
+    }
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+    *req_id = r->id;
+  }
+  s->cv_work.notify_one();
+  return DC_OK;
+}
+
+extern "C" dc_status dc_serve_wait(dc_server* s, long long id, int timeout_ms, double* latency_s) {
+  if (!s) return DC_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return DC_EINVAL;
+  Request* r = it->second;
+  const auto pred = [r] { return r->state >= 2; };
+  if (timeout_ms < 0) s->cv_done.wait(lk, pred);
+  else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return DC_ETIMEOUT;
+  const dc_status st = r->state == 4 ? DC_ECANCELLED : r->status;
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  s->reqs.erase(it);
+  delete r;
+  return st;
+}
+
+extern "C" dc_status dc_serve_cancel(dc_server* s, long long id) {
+  if (!s) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return DC_EINVAL;
+  Request* r = it->second;
+  if (r->state != 0) return DC_EBUSY;     // already admitted to the GPU
+  s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+  r->state = 4;
+  r->t_done = Clock::now();
+  s->cv_done.notify_all();
+  return DC_OK;
+}
+
+extern "C" dc_status dc_serve_stats(dc_server* s, double* p50_s, double* p99_s, double* msamples_per_s,
+                                    long long* completed) {
+  if (!s) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  std::vector<double> l = s->latencies;
+  auto pct = [&l](double q) {
+    if (l.empty()) return 0.0;
+    const size_t k = std::min(l.size() - 1, (size_t)(q * (l.size() - 1) + 0.5));
+    std::nth_element(l.begin(), l.begin() + k, l.end());
+    return l[k];
+  };
+  if (p50_s) *p50_s = pct(0.50);
+  if (p99_s) *p99_s = pct(0.99);
+  if (msamples_per_s) {
+    const double dt = s->have_first ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
+    *msamples_per_s = dt > 0 ? s->done_samples / dt / 1e6 : 0.0;
+  }
+  if (completed) *completed = s->completed;
+  return DC_OK;
+}
+
+extern "C" dc_status dc_serve_stop(dc_server* s) {
+  if (!s) return DC_EINVAL;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->th.joinable()) s->th.join();
+  cudaSetDevice(s->device);
+  for (Slot& sl : s->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.ctx) dc_destroy(sl.ctx);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.in_dev) cudaFree(sl.in_dev);
+    if (sl.out_dev) cudaFree(sl.out_dev);
+    if (sl.in_host) cudaFreeHost(sl.in_host);
+    if (sl.out_host) cudaFreeHost(sl.out_host);
+  }
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+  return DC_OK;
+}
