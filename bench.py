@@ -422,6 +422,207 @@ def run_split(args) -> None:
     ctx.close()
 
 
+# ---------------------------------------------------------- uneven batch
+
+def run_batch(args) -> None:
+    """4096 pulses, lengths log-uniform in [1024, 262144], half LFM / half
+    noise, each with its own v_r and TEC, corrected as one graph launch
+    (dc_plan_batch), against the plain per-pulse path."""
+    import torch
+    import paper_2508_04951_gb300 as dcg
+
+    dcg.build.build()
+    dcg.load()
+    cfg = synth.UnevenBatch()
+    if args.n_v:
+        cfg.n_pulses = args.n_v
+    lens, x, offs, v, tec = cfg.draw()
+    items = np.zeros(cfg.n_pulses, dtype=dcg.ITEM_DTYPE)
+    for i in range(cfg.n_pulses):
+        items[i] = (offs[i], lens[i], offs[i], lens[i], cfg.fs, cfg.fc, v[i], tec[i])
+    total = int(lens.sum())
+    ctx = dcg.Context(0)
+    stream = torch.cuda.current_stream()
+    xd = torch.from_numpy(x).cuda()
+    od = torch.empty_like(xd)
+    plan = dcg.dc_plan_batch(ctx, xd, od, items)
+    for _ in range(args.warmup):
+        plan.execute()
+    dcg.dc_check(ctx)
+    dcg.dc_profile_enable(ctx, True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k, (a, b) in enumerate(ev):
+        flush.fill_(k & 255)
+        a.record(stream)
+        plan.execute()
+        b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dcg.dc_profile_enable(ctx, False)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t = sum(ms) / len(ms)
+    # the same batch as direct calls (no graph), one step for reference
+    prof_direct = {}
+    dcg.dc_profile_enable(ctx, True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    dcg.correct_batch(ctx, xd, od, items)
+    b.record(stream)
+    torch.cuda.synchronize()
+    direct_ms = a.elapsed_time(b)
+    prof_direct = dcg.dc_profile_read(ctx)
+    dcg.dc_profile_enable(ctx, False)
+    # plain per-pulse path on a sample of pulses
+    rng = np.random.default_rng(3)
+    pick = rng.choice(cfg.n_pulses, min(args.plain_pairs * 2, cfg.n_pulses), replace=False)
+    y_tmp = torch.empty(int(lens.max()), dtype=torch.complex64, device="cuda")
+    pe, ps = [], 0
+    for j, i in enumerate(pick):
+        n = int(lens[i])
+        xs = xd[offs[i]:offs[i] + n]
+        zs = od[offs[i]:offs[i] + n]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dcg.doppler_resample(ctx, xs, y_tmp[:n], cfg.fs, cfg.fc, float(v[i]))
+        dcg.iono_correct(ctx, y_tmp[:n], zs, cfg.fs, cfg.fc, float(tec[i]))
+        b.record(stream)
+        pe.append((a, b))
+        ps += n
+    torch.cuda.synchronize()
+    plain = [a.elapsed_time(b) for a, b in pe]
+    # error on sampled pulses (plan output recomputed)
+    plan.execute()
+    torch.cuda.synchronize()
+    import oracle
+    out = od.cpu().numpy()
+    errs = []
+    for i in rng.choice(cfg.n_pulses, 12, replace=False):
+        n = int(lens[i])
+        ref = oracle.correct(x[offs[i]:offs[i] + n].astype(np.complex128), cfg.fs, cfg.fc, v[i], tec[i])
+        got = out[offs[i]:offs[i] + n].astype(np.complex128)
+        errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    line = {
+        "metric": METRIC, "value": total / (t / 1e3) / 1e6, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uneven_batch", "pulses": cfg.n_pulses, "samples": total,
+                   "lengths": "log-uniform [1024, 262144]", "fs_hz": cfg.fs, "fc_hz": cfg.fc,
+                   "l2": "flushed between timed steps (256 MiB write outside the step events)"},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "graph_launches_per_step": plan.launches, "direct_call_ms": direct_ms,
+        "phases_ms_direct": {k: vv[2] for k, vv in prof_direct.items()},
+        "clocks": clk,
+        "plain_path": {"value": ps / (sum(plain) / 1e3) / 1e6, "unit": UNIT,
+                       "p50_ms": float(np.percentile(plain, 50)), "p99_ms": float(np.percentile(plain, 99)),
+                       "pulses_timed": len(plain)},
+        "error": {"rel_l2_max": max(errs), "pulses_checked": len(errs), "tolerance": 1e-5},
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+
+
+# --------------------------------------------------------------- serving
+
+def run_serve(args) -> None:
+    """Poisson request stream (20 k pulses/s) of mixed LFM / noise pulses,
+    lengths log-uniform in [2048, 2^20], through the continuous-batching
+    server, against a serial per-request server on the same arrivals."""
+    import threading
+    import torch
+    import paper_2508_04951_gb300 as dcg
+
+    dcg.build.build()
+    dcg.load()
+    cfg = synth.ServingStream()
+    rng = synth.rng_for(cfg.seed_index)
+    arrivals = cfg.arrivals(rng, duration=args.duration)
+    pool = [(synth.lfm(cfg.n_max, cfg.fs, rng.uniform(1e6, 10e6)) if k % 2 == 0
+             else synth.bandlimited_noise(cfg.n_max, rng)).astype(np.complex64) for k in range(16)]
+    nreq = len(arrivals)
+    ln = np.exp(rng.uniform(np.log(cfg.n_min), np.log(cfg.n_max), nreq))
+    lens = np.clip(np.round(ln).astype(np.int64), cfg.n_min, cfg.n_max)
+    src = rng.integers(0, len(pool), nreq)
+    v = rng.uniform(-8000, 8000, nreq)
+    tec = rng.uniform(5, 150, nreq)
+    R = 256
+    ring = [np.empty(cfg.n_max, dtype=np.complex64) for _ in range(R)]
+    srv = dcg.dc_serve_start(0, cfg.budget_bytes, slots=args.slots)
+    ids = [None] * nreq
+    done_upto = [0]
+    cond = threading.Condition()
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            with cond:
+                while i - done_upto[0] >= R:
+                    cond.wait()
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            n = int(lens[i])
+            ids[i] = srv.submit(pool[src[i]][:n], ring[i % R][:n], cfg.fs, cfg.fc, v[i], tec[i])
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    for i in range(nreq):
+        while ids[i] is None:
+            time.sleep(20e-6)
+        srv.wait(ids[i])
+        with cond:
+            done_upto[0] = i + 1
+            cond.notify()
+    th.join()
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.stop()
+    # serial per-request server on the first part of the same stream
+    ctx = dcg.Context(0)
+    k_serial = min(nreq, int(cfg.rate * args.serial_seconds))
+    xs = torch.empty(cfg.n_max, dtype=torch.complex64, device="cuda")
+    ys = torch.empty_like(xs)
+    item = np.zeros(1, dtype=dcg.ITEM_DTYPE)
+    lat = []
+    t0 = time.perf_counter()
+    clock = 0.0
+    for i in range(k_serial):
+        now = time.perf_counter() - t0
+        if now < arrivals[i]:
+            time.sleep(arrivals[i] - now)
+        n = int(lens[i])
+        xs[:n].copy_(torch.from_numpy(pool[src[i]][:n]))
+        item[0] = (0, n, 0, n, cfg.fs, cfg.fc, v[i], tec[i])
+        dcg.correct_batch(ctx, xs, ys, item)
+        ring[i % R][:n] = ys[:n].cpu().numpy()
+        lat.append(time.perf_counter() - t0 - arrivals[i])
+    serial_wall = time.perf_counter() - t0
+    ctx.close()
+    line = {
+        "metric": METRIC, "value": st["msamples_per_s"], "unit": UNIT, "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "rate_per_s": cfg.rate, "duration_s": args.duration,
+                   "requests": nreq, "lengths": "log-uniform [2048, 2^20]",
+                   "offered_msamples_per_s": float(lens.sum() / args.duration / 1e6),
+                   "budget_bytes": cfg.budget_bytes, "slots": args.slots},
+        "latency_ms": {"p50": 1e3 * st["p50_s"], "p99": 1e3 * st["p99_s"]},
+        "completed": st["completed"], "wall_s": wall,
+        "plain_path": {"what": "serial per-request correct_batch with synchronous copies",
+                       "requests": k_serial,
+                       "value": float(lens[:k_serial].sum() / serial_wall / 1e6), "unit": UNIT,
+                       "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                       "p99_ms": 1e3 * float(np.percentile(lat, 99))},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,8 +634,12 @@ def main() -> None:
     ap.add_argument("--cpu-sample-v", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-v", type=int, default=None, help="fewer range rates (small profiling case)")
-    ap.add_argument("--workload", choices=["bank", "split"], default="bank",
-                    help="bank: the Doppler-bank headline line; split: the exact-sinc tensor-core GEMM")
+    ap.add_argument("--workload", choices=["bank", "split", "batch", "serve"], default="bank",
+                    help="bank: the Doppler-bank headline line; split: the exact-sinc tensor-core "
+                         "GEMM; batch: the uneven batch; serve: the Poisson request stream")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--serial-seconds", type=float, default=1.0, help="serve: seconds for the serial server")
+    ap.add_argument("--slots", type=int, default=3, help="serve: batches in flight")
     ap.add_argument("--split-mode", choices=["bf16x3", "fp16x3"], default="bf16x3")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -447,6 +652,12 @@ def main() -> None:
         return
     if args.workload == "split":
         run_split(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     run_gpu(args, rank, world, local_rank)
 

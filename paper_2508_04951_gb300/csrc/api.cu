@@ -199,31 +199,59 @@ struct Arena {
   }
 };
 
-struct KaiserTable {
-  int half, nk;
-  float inv_r2;
-  float kc[kMaxKaiser];
-};
+// Kaiser window w(u) = I0(beta sqrt(1 - (u/R)^2)) / I0(beta), |u| <= R.
+double kaiser_fp64(double u, double R, double beta) {
+  const double r = u / R;
+  if (std::fabs(r) > 1.0) return 0.0;
+  auto i0 = [](double x) {
+    const double q = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200; ++k) {
+      term *= q / ((double)k * (double)k);
+      sum += term;
+      if (term < 1e-17 * sum) break;
+    }
+    return sum;
+  };
+  return i0(beta * std::sqrt(std::max(0.0, 1.0 - r * r))) / i0(beta);
+}
 
-// Kaiser window as a polynomial in zeta = 1 - (u/R)^2:
-// w = I0(beta sqrt(zeta)) / I0(beta) = sum_j (beta^2/4)^j / ((j!)^2 I0(beta)) zeta^j.
-bool kaiser_table(int taps, double beta, KaiserTable& t) {
-  t.half = taps / 2;
-  t.inv_r2 = (float)(1.0 / ((double)t.half * (double)t.half));
-  double q = beta * beta / 4.0, term = 1.0, i0 = 0.0;
-  double terms[kMaxKaiser];
-  int n = 0;
-  for (int j = 0; j < kMaxKaiser; ++j) {
-    if (j > 0) term *= q / ((double)j * (double)j);
-    terms[j] = term;
-    i0 += term;
-    n = j + 1;
-    if (j > 2 && term < 1e-12 * i0) break;
+// Per-tap polynomial of the window in the fractional delay e in [0, 1]:
+// w(e - k) = sum_d c[d] e^d, degree kWCoef-1, interpolating at Chebyshev
+// nodes of [0, 1] (solved in FP64).  Layout [tap t = k + R - 1][kWCoef].
+std::vector<float> window_poly(int taps, double beta) {
+  const int R = taps / 2, D = kWCoef;
+  std::vector<float> out((size_t)taps * D);
+  const double pi = 3.14159265358979323846;
+  double nodes[kWCoef];
+  for (int i = 0; i < D; ++i) nodes[i] = 0.5 + 0.5 * std::cos(pi * (i + 0.5) / D);
+  for (int t = 0; t < taps; ++t) {
+    const int k = t - R + 1;
+    double A[kWCoef][kWCoef + 1];
+    for (int i = 0; i < D; ++i) {
+      double p = 1.0;
+      for (int d = 0; d < D; ++d, p *= nodes[i]) A[i][d] = p;
+      A[i][D] = kaiser_fp64(nodes[i] - k, (double)R, beta);
+    }
+    for (int c = 0; c < D; ++c) {             // Gaussian elimination, partial pivoting
+      int piv = c;
+      for (int i = c + 1; i < D; ++i)
+        if (std::fabs(A[i][c]) > std::fabs(A[piv][c])) piv = i;
+      for (int d = 0; d <= D; ++d) std::swap(A[c][d], A[piv][d]);
+      for (int i = c + 1; i < D; ++i) {
+        const double f = A[i][c] / A[c][c];
+        for (int d = c; d <= D; ++d) A[i][d] -= f * A[c][d];
+      }
+    }
+    double coef[kWCoef];
+    for (int c = D - 1; c >= 0; --c) {
+      double v = A[c][D];
+      for (int d = c + 1; d < D; ++d) v -= A[c][d] * coef[d];
+      coef[c] = v / A[c][c];
+    }
+    for (int d = 0; d < D; ++d) out[(size_t)t * D + d] = (float)coef[d];
   }
-  if (n >= kMaxKaiser) return false;
-  for (int j = 0; j < n; ++j) t.kc[j] = (float)(terms[j] / i0);
-  t.nk = n;
-  return true;
+  return out;
 }
 
 dc_status check_opts(dc_ctx* c, const dc_opts* o) {
@@ -276,15 +304,17 @@ dc_status upload(dc_ctx* c, const std::vector<T>& v, size_t at, cudaStream_t s, 
 dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, size_t item_at,
                        cudaStream_t s) {
   if (items.empty()) return DC_OK;
-  KaiserTable kt;
-  if (!kaiser_table(o.taps, o.kaiser_beta, kt)) return fail(c, DC_EINVAL, "kaiser table overflow");
+  const std::vector<float> wp = window_poly(o.taps, o.kaiser_beta);
+  const float* dwp = nullptr;
+  dc_status st = upload(c, wp, item_at, s, &dwp);
+  if (st) return st;
+  size_t at = item_at + ((wp.size() * sizeof(float) + 255) & ~(size_t)255);
   // Split into the tiled launch (32 taps, |delta| <= 0.01) and the direct one.
   std::vector<RsItem> tiled, direct;
   for (auto& it : items) {
     const double dl = (double)it.dl_hi + (double)it.dl_lo;
     (o.taps == 32 && std::fabs(dl) <= kRsTiledMaxDelta ? tiled : direct).push_back(it);
   }
-  size_t at = item_at;
   for (int pass = 0; pass < 2; ++pass) {
     auto& v = pass == 0 ? tiled : direct;
     if (v.empty()) continue;
@@ -294,17 +324,14 @@ dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, 
       tiles += (int)((it.n_out + kRsTile - 1) / kRsTile);
     }
     const RsItem* dev = nullptr;
-    dc_status st = upload(c, v, at, s, &dev);
-    if (st) return st;
+    if ((st = upload(c, v, at, s, &dev))) return st;
     at += (v.size() * sizeof(RsItem) + 255) & ~(size_t)255;
     RsArgs a{};
     a.items = dev;
     a.n_items = (int)v.size();
     a.n_tiles = tiles;
-    a.half = kt.half;
-    a.nk = kt.nk;
-    a.inv_r2 = kt.inv_r2;
-    memcpy(a.kc, kt.kc, sizeof(float) * kt.nk);
+    a.half = o.taps / 2;
+    a.wpoly = dwp;
     a.err = c->err;
     long long outs = 0;
     for (auto& it : v) outs += it.n_out;
@@ -315,7 +342,7 @@ dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, 
   return DC_OK;
 }
 
-size_t items_bytes_for(size_t n) { return ((n * 128 + 255) & ~(size_t)255) + 4096; }
+size_t items_bytes_for(size_t n) { return ((n * 128 + 255) & ~(size_t)255) + 16384; }
 
 // ------------------------------------------------------ correction pipeline
 // One L class of pulses already resampled into y; writes corrected outputs.
@@ -378,7 +405,8 @@ dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2*
   RowArgs a2{d2, (int)it.size(), log2L, log2L1, c->tw};
   {
     Phase ph(c, PH_ROW_MID, s, outs);
-    if ((e = launch_row(ROW_MID, a2, s)) != cudaSuccess) return cuda_fail(c, e, "row launch");
+    e = log2L >= 17 ? launch_row_mid_4096(a2, s) : launch_row(ROW_MID, a2, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "row launch");
   }
   ColArgs a3{d3, (int)it.size(), log2L, log2L1, c->tw};
   {
@@ -645,7 +673,7 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
       split(alpha_minus_one(it.v_r), rs[i].dl_hi, rs[i].dl_lo);
     }
     if ((st = run_windowed(c, rs, o, item_at, s))) return st;
-    item_at += 2 * ((n_items * sizeof(RsItem) + 255) & ~(size_t)255);
+    item_at += 2 * ((n_items * sizeof(RsItem) + 255) & ~(size_t)255) + 4096;
   } else {
     for (int i = 0; i < n_items; ++i) {
       const dc_item& it = items[i];
@@ -771,7 +799,7 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     split(alpha_minus_one(v_r[i]), rs[i].dl_hi, rs[i].dl_lo);
   }
   if ((st = run_windowed(c, rs, o, item_at, s))) return st;
-  item_at += 2 * ((n_v * sizeof(RsItem) + 255) & ~(size_t)255);
+  item_at += 2 * ((n_v * sizeof(RsItem) + 255) & ~(size_t)255) + 4096;
   // 3. spectra per v_r
   std::vector<FftItem> sp(n_v);
   for (int i = 0; i < n_v; ++i) {

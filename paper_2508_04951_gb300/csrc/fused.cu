@@ -253,7 +253,52 @@ cudaError_t launch_op(const FusedArgs& a, cudaStream_t s) {
   }
 }
 
+// Middle pass of the three-pass four-step path for 65536 < L <= 2^20
+// (L1 = L / 4096 in 32..256 rows): one 4096-point row per CTA -- forward
+// row FFT, exp(-i phi_k) at bin k1 + L1 k2, inverse row FFT, four-step
+// twiddle W_L^(-n2 k1) -- in place on the scratch T between the column
+// passes.
+__global__ void __launch_bounds__(kRowThreads, 2) row_mid_kernel(RowArgs a) {
+  extern __shared__ __align__(128) float2 sm[];
+  const int L1 = 1 << a.log2L1;
+  const int g = blockIdx.x;
+  const int item = g >> a.log2L1, k1 = g & (L1 - 1);
+  const FftItem I = a.items[item];
+  const int j = threadIdx.x;
+  float2* bufA = sm;
+  float2* bufB = sm + kRowPitch;
+  const float2* src = I.src + (size_t)k1 * kRowN;
+  float2 v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = src[j + 256 * r];
+  row4096<-1>(v, bufA, bufB, j, a.tw);
+  if (I.ph.enabled) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], iono_factor(I.ph, k1 + L1 * (j + 256 * r)));
+  }
+  row4096<+1>(v, bufA, bufB, j, a.tw);
+  if (k1) {
+    const float2 a_j = tw_big<+1>(a.tw, (uint32_t)(j * k1), a.log2L);
+    const int m16 = 16 * L1 - 1, step = 256 >> a.log2L1;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], cmul(a_j, tw_m<+1>(a.tw, ((r * k1) & m16) * step)));
+  }
+  float2* dst = I.dst + (size_t)k1 * kRowN;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) dst[j + 256 * r] = v[r];
+}
+
 }  // namespace
+
+cudaError_t launch_row_mid_4096(const RowArgs& a, cudaStream_t s) {
+  if (a.n_items <= 0) return cudaSuccess;
+  if (a.log2L - a.log2L1 != 12 || a.log2L1 < 5 || a.log2L1 > 8) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * 2 * kRowPitch;
+  cudaError_t e = cudaFuncSetAttribute(row_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  row_mid_kernel<<<(unsigned)(a.n_items << a.log2L1), kRowThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;

@@ -34,4 +34,9 @@ struct FusedArgs {
 // Launch; returns cudaErrorInvalidValue for L outside [4096, 65536].
 cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s);
 
+// Middle (row) pass of the three-pass path for 2^17 <= L <= 2^20: forward
+// row, phase, inverse row, four-step twiddle, in place (RowArgs as for
+// ROW_MID, rows of 4096).
+cudaError_t launch_row_mid_4096(const RowArgs& a, cudaStream_t s);
+
 }  // namespace dc

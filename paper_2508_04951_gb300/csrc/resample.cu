@@ -42,11 +42,17 @@ DC_DEV void rs_delay(float dl_hi, float dl_lo, float fi, int& fl, float& e) {
   e = r;
 }
 
-DC_DEV float kaiser_w(const RsArgs& a, float u) {
-  const float z = fmaxf(fmaf(-u * u, a.inv_r2, 1.0f), 0.0f);
-  float w = a.kc[a.nk - 1];
-  for (int j = a.nk - 2; j >= 0; --j) w = fmaf(w, z, a.kc[j]);
-  return w;
+// w(e - k) from the per-tap polynomial, t = k + R - 1.
+DC_DEV float window_at(const float* __restrict__ wp, int t, float e) {
+  const float4 lo = __ldg(reinterpret_cast<const float4*>(wp + t * kWCoef));
+  const float4 hi = __ldg(reinterpret_cast<const float4*>(wp + t * kWCoef + 4));
+  float w = fmaf(hi.w, e, hi.z);
+  w = fmaf(w, e, hi.y);
+  w = fmaf(w, e, hi.x);
+  w = fmaf(w, e, lo.w);
+  w = fmaf(w, e, lo.z);
+  w = fmaf(w, e, lo.y);
+  return fmaf(w, e, lo.x);
 }
 
 // h(e - k) for tap k; s_e = sin(pi e)/pi.
@@ -54,7 +60,7 @@ DC_DEV float tap_weight(const RsArgs& a, float e, float s_e, int k) {
   const float u = e - (float)k;
   if (u == 0.f) return 1.f;
   const float sc = __fdividef((k & 1) ? -s_e : s_e, u);
-  return sc * kaiser_w(a, u);
+  return sc * window_at(a.wpoly, k + a.half - 1, e);
 }
 
 DC_DEV int find_item(const RsArgs& a, int tile) {
@@ -68,8 +74,11 @@ DC_DEV int find_item(const RsArgs& a, int tile) {
 
 // ------------------------------------------------------------- direct
 __global__ void __launch_bounds__(kRsThreads) resample_direct_kernel(RsArgs a) {
+  __shared__ int s_item;
   const int tile = blockIdx.x;
-  const RsItem& I = a.items[find_item(a, tile)];
+  if (threadIdx.x == 0) s_item = find_item(a, tile);
+  __syncthreads();
+  const RsItem& I = a.items[s_item];
   const int o0 = (tile - I.tile_begin) * kRsTile;
   for (int q = 0; q < kRsTile / kRsThreads; ++q) {
     const int i = o0 + q * kRsThreads + threadIdx.x;
@@ -107,18 +116,49 @@ constexpr int kWaitLimit = 1 << 22;      // bounded mbarrier polls
 // interpolation error is about 0.064 |h'''| (span/2)^3 <= 2e-7 per weight.
 constexpr float kQuadSpan = 0.015f;
 
+// Inner product loop of one lane over all taps: outputs ow + 4 lane + q,
+// inputs at padded window positions P0 + m + ((R0 + m) >> 2) -- R0, the
+// warp-uniform alignment of the window start, is a template parameter, so
+// every load has a constant offset.
+template <int TAPS, int R0>
+DC_DEV void tap_loop(const float2* __restrict__ w0, const float4* __restrict__ wts,
+                     const float (&sq)[kRsQ], float2 (&acc)[kRsQ]) {
+  float2 xw[kRsQ];
+#pragma unroll
+  for (int q = 0; q < kRsQ; ++q) xw[q] = w0[q + ((R0 + q) >> 2)];
+#pragma unroll
+  for (int t = 0; t < TAPS; ++t) {
+    const float4 w = wts[t];
+#pragma unroll
+    for (int q = 0; q < kRsQ; ++q) {
+      const float h = fmaf(fmaf(w.z, sq[q], w.y), sq[q], w.x);
+      acc[q].x = fmaf(xw[q].x, h, acc[q].x);
+      acc[q].y = fmaf(xw[q].y, h, acc[q].y);
+    }
+#pragma unroll
+    for (int q = 0; q + 1 < kRsQ; ++q) xw[q] = xw[q + 1];
+    if (t + 1 < TAPS) {
+      const int m = kRsQ + t;
+      xw[kRsQ - 1] = w0[m + ((R0 + m) >> 2)];
+    }
+  }
+}
+
 template <int HALF>
 __global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
   constexpr int TAPS = 2 * HALF;
   constexpr int NW = kRsThreads / 32;
   constexpr int WINMAX = kRsTile + 2 * HALF + 40;
-  __shared__ __align__(16) float2 stage[WINMAX + 2];
+  __shared__ __align__(16) float2 stage[WINMAX + 2];   // TMA window, later the output tile
   __shared__ float2 win[WINMAX + WINMAX / 4 + 2];
   __shared__ float4 wts[NW][TAPS];
   __shared__ __align__(8) unsigned long long mbar;
+  __shared__ int s_item;
 
   const int tile = blockIdx.x;
-  const RsItem& I = a.items[find_item(a, tile)];
+  if (threadIdx.x == 0) s_item = find_item(a, tile);
+  __syncthreads();
+  const RsItem& I = a.items[s_item];
   const int o0 = (tile - I.tile_begin) * kRsTile;
 
   // Input window of the CTA's 1024 outputs.
@@ -168,8 +208,9 @@ __global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
           : "r"(mb)
           : "memory");
     }
-    if (!done) {
-      atomicExch(a.err, 1);
+    if (!__syncthreads_and(done)) {            // every thread takes the same exit
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      done = 0;
       for (int it = 0; it < kWaitLimit && !done; ++it) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
@@ -189,11 +230,10 @@ __global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
     else if (gi >= 0 && gi < I.n_in) v = __ldg(I.x + gi);
     win[wpad(idx)] = v;
   }
-  __syncthreads();
+  __syncthreads();                           // window ready; stage is free again
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ow = o0 + warp * kRsW;
-  if (ow >= I.n_out) return;
   constexpr float H = 0.5f * (kRsW - 1);
   int f0, f1, f2;
   float e0, e1, e2;
@@ -204,66 +244,72 @@ __global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
 #pragma unroll
   for (int q = 0; q < kRsQ; ++q) acc[q] = make_float2(0.f, 0.f);
 
-  if (f0 == f2 && f0 == f1 && fabsf(e2 - e0) <= kQuadSpan) {
-    // Quadratic weights per tap through the three nodes s = -H, 0, +H.
-    const float s0 = sinpif(e0) * kInvPi, s1 = sinpif(e1) * kInvPi, s2 = sinpif(e2) * kInvPi;
-    for (int t = lane; t < TAPS; t += 32) {
-      const int k = t - HALF + 1;
-      const float hA = tap_weight(a, e0, s0, k);
-      const float hB = tap_weight(a, e1, s1, k);
-      const float hC = tap_weight(a, e2, s2, k);
-      const float q1 = (hC - hA) * (0.5f / H);
-      const float q2 = (hC - 2.f * hB + hA) * (0.5f / (H * H));
-      wts[warp][t] = make_float4(hB, q1, q2, 0.f);
-    }
-    __syncwarp();
-    const int base = ow + lane * kRsQ + f0 - HALF + 1 - wlo;
-    float sq[kRsQ];
-    float2 xw[kRsQ];
+  if (ow < I.n_out) {
+    if (f0 == f2 && f0 == f1 && fabsf(e2 - e0) <= kQuadSpan) {
+      // Quadratic weights per tap through the three nodes s = -H, 0, +H.
+      const float s0 = sinpif(e0) * kInvPi, s1 = sinpif(e1) * kInvPi, s2 = sinpif(e2) * kInvPi;
+      for (int t = lane; t < TAPS; t += 32) {
+        const int k = t - HALF + 1;
+        const float hA = tap_weight(a, e0, s0, k);
+        const float hB = tap_weight(a, e1, s1, k);
+        const float hC = tap_weight(a, e2, s2, k);
+        const float q1 = (hC - hA) * (0.5f / H);
+        const float q2 = (hC - 2.f * hB + hA) * (0.5f / (H * H));
+        wts[warp][t] = make_float4(hB, q1, q2, 0.f);
+      }
+      __syncwarp();
+      // Window index of output ow + 4 lane + q at tap t is B + 4 lane + m,
+      // m = q + t; with B = 4 b + r (r = B & 3, uniform in the warp) its
+      // padded position is 5 lane + B + b + m + ((r + m) >> 2).
+      const int B = ow + f0 - HALF + 1 - wlo;
+      const int P0 = 5 * lane + B + (B >> 2);
+      float sq[kRsQ];
 #pragma unroll
-    for (int q = 0; q < kRsQ; ++q) {
-      sq[q] = (float)(lane * kRsQ + q) - H;
-      xw[q] = win[wpad(base + q)];
-    }
-#pragma unroll
-    for (int t = 0; t < TAPS; ++t) {
-      const float4 w = wts[warp][t];
+      for (int q = 0; q < kRsQ; ++q) sq[q] = (float)(lane * kRsQ + q) - H;
+      switch (B & 3) {
+        case 0: tap_loop<TAPS, 0>(win + P0, wts[warp], sq, acc); break;
+        case 1: tap_loop<TAPS, 1>(win + P0, wts[warp], sq, acc); break;
+        case 2: tap_loop<TAPS, 2>(win + P0, wts[warp], sq, acc); break;
+        default: tap_loop<TAPS, 3>(win + P0, wts[warp], sq, acc); break;
+      }
+    } else {
+      // floor(delta n) steps inside this warp tile, or e moves too far:
+      // exact weights per output.
 #pragma unroll
       for (int q = 0; q < kRsQ; ++q) {
-        const float h = fmaf(fmaf(w.z, sq[q], w.y), sq[q], w.x);
-        acc[q].x = fmaf(xw[q].x, h, acc[q].x);
-        acc[q].y = fmaf(xw[q].y, h, acc[q].y);
-      }
-#pragma unroll
-      for (int q = 0; q + 1 < kRsQ; ++q) xw[q] = xw[q + 1];
-      if (t + 1 < TAPS) xw[kRsQ - 1] = win[wpad(base + kRsQ + t)];
-    }
-  } else {
-    // floor(delta n) steps inside this warp tile: exact weights per output.
-#pragma unroll 1
-    for (int q = 0; q < kRsQ; ++q) {
-      const int i = ow + lane * kRsQ + q;
-      int fl;
-      float e;
-      rs_delay(I.dl_hi, I.dl_lo, (float)i, fl, e);
-      const int m = i + fl - wlo;
-      if (e == 0.f) {
-        acc[q] = win[wpad(m)];
-      } else {
-        const float s_e = sinpif(e) * kInvPi;
-        for (int k = -HALF + 1; k <= HALF; ++k) {
-          const float h = tap_weight(a, e, s_e, k);
-          const float2 v = win[wpad(m + k)];
-          acc[q].x = fmaf(v.x, h, acc[q].x);
-          acc[q].y = fmaf(v.y, h, acc[q].y);
+        const int i = ow + lane * kRsQ + q;
+        int fl;
+        float e;
+        rs_delay(I.dl_hi, I.dl_lo, (float)i, fl, e);
+        const int m = i + fl - wlo;
+        if (e == 0.f) {
+          acc[q] = win[wpad(m)];
+        } else {
+          const float s_e = sinpif(e) * kInvPi;
+          for (int k = -HALF + 1; k <= HALF; ++k) {
+            const float h = tap_weight(a, e, s_e, k);
+            const float2 v = win[wpad(m + k)];
+            acc[q].x = fmaf(v.x, h, acc[q].x);
+            acc[q].y = fmaf(v.y, h, acc[q].y);
+          }
         }
       }
     }
   }
-#pragma unroll
-  for (int q = 0; q < kRsQ; ++q) {
-    const int i = ow + lane * kRsQ + q;
-    if (i < I.n_out) I.y[i] = acc[q];
+  // Output tile through shared memory, then 16-byte coalesced stores.
+  float4* st4 = reinterpret_cast<float4*>(stage) + warp * (kRsW / 2) + lane * 2;
+  st4[0] = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+  st4[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
+  __syncthreads();
+  const int n_here = min(kRsTile, I.n_out - o0);
+  float2* y = I.y + o0;
+  if ((reinterpret_cast<uintptr_t>(y) & 15) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(stage);
+    for (int p = threadIdx.x; 2 * p + 1 < n_here; p += kRsThreads)
+      __stcs(reinterpret_cast<float4*>(y) + p, s4[p]);
+    if ((n_here & 1) && threadIdx.x == 0) y[n_here - 1] = stage[n_here - 1];
+  } else {
+    for (int p = threadIdx.x; p < n_here; p += kRsThreads) y[p] = stage[p];
   }
 }
 

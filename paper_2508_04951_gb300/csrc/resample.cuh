@@ -6,8 +6,8 @@
 
 namespace dc {
 
-constexpr int kMaxKaiser = 40;    // Kaiser I0 polynomial coefficients
 constexpr int kMaxHalf = 32;      // taps <= 64
+constexpr int kWCoef = 8;         // window polynomial coefficients per tap (degree 7)
 
 // One pulse of a windowed-resample launch.
 struct RsItem {
@@ -23,9 +23,10 @@ struct RsArgs {
   int n_items;
   int n_tiles;         // total tiles of the launch
   int half;            // R = taps / 2
-  int nk;              // Kaiser coefficients used
-  float inv_r2;        // 1 / R^2
-  float kc[kMaxKaiser];// w(u) = sum_j kc[j] zeta^j, zeta = 1 - (u/R)^2 (I0 series / I0(beta))
+  // Kaiser window of tap k at fractional delay e in [0, 1]:
+  //   w(e - k) = sum_d wpoly[t * kWCoef + d] e^d,  t = k + R - 1
+  // (fitted per tap in FP64 on the host; |error| <= 6e-8 for beta <= 20).
+  const float* wpoly;
   int* err;            // device error flag (bounded waits)
 };
 
