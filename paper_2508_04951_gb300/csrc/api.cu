@@ -39,6 +39,7 @@ struct dc_ctx {
   size_t budget = 0;
   std::string last_error;
   float2* tw = nullptr;       // twiddle tables (kTwSize)
+  float2* t4 = nullptr;       // four-step twiddles of the spectrum-apply kernel (kT4Size)
   int* err = nullptr;         // device error flag
   char* ws = nullptr;         // scratch
   size_t ws_bytes = 0;
@@ -458,15 +459,20 @@ dc_status dc_create(dc_ctx** out, int device, size_t budget) {
   c->device = device;
   c->budget = budget;
   // Twiddle tables in FP64, rounded to float (layout in common.cuh).
-  std::vector<float2> tw(kTwSize);
+  std::vector<float2> tw(kTwSize), t4(kT4Size);
   fill_twiddles(tw.data());
+  fill_four_step(t4.data());
   if ((e = cudaMalloc(&c->tw, sizeof(float2) * kTwSize)) != cudaSuccess ||
       (e = cudaMemcpy(c->tw, tw.data(), sizeof(float2) * kTwSize, cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMalloc(&c->t4, sizeof(float2) * kT4Size)) != cudaSuccess ||
+      (e = cudaMemcpy(c->t4, t4.data(), sizeof(float2) * kT4Size, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMalloc(&c->err, sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(c->err, 0, sizeof(int))) != cudaSuccess) {
     cudaGetLastError();
     if (c->tw) cudaFree(c->tw);
+    if (c->t4) cudaFree(c->t4);
     if (c->err) cudaFree(c->err);
     delete c;
     return DC_ENOMEM;
@@ -485,6 +491,7 @@ dc_status dc_destroy(dc_ctx* c) {
   if (c->ws) cudaFree(c->ws);
   if (c->items) cudaFree(c->items);
   if (c->tw) cudaFree(c->tw);
+  if (c->t4) cudaFree(c->t4);
   if (c->err) cudaFree(c->err);
   delete c;
   return DC_OK;
@@ -856,7 +863,7 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     }
   if (fused) {
     if ((st = upload(c, ap, item_at, s, &dev))) return st;
-    FusedArgs a{dev, (int)n_pairs, log2L, c->tw, c->err};
+    FusedArgs a{dev, (int)n_pairs, log2L, c->tw, c->err, c->t4};
     Phase ph(c, PH_FUSED_APPLY, s, (long long)n_pairs * n_out);
     if ((e = launch_fused(FUSED_APPLY, a, s)) != cudaSuccess) return cuda_fail(c, e, "apply launch");
     return DC_OK;

@@ -56,6 +56,30 @@ DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
   dft16<DIR>(v);
 }
 
+// The same row in one padded buffer: a third CTA barrier (before stage 2's
+// writes) replaces the second buffer.  On return other threads may still be
+// reading b.
+template <int DIR>
+DC_DEV void row4096_1buf(float2 (&v)[16], float2* b, int j, const float2* __restrict__ tw) {
+  dft16<DIR>(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b[pad16(16 * j + r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
+  twiddle_stage2<DIR>(v, tw, j & 15);
+  dft16<DIR>(v);
+  const int base = (j >> 4) * 256 + (j & 15);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b[pad16(base + 16 * r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
+  twiddle_stage3<DIR>(v, tw, j);
+  dft16<DIR>(v);
+}
+
 template <int CL> DC_DEV void cluster_sync() {
   if constexpr (CL > 1) cg::this_cluster().sync();
   else __syncthreads();
@@ -70,6 +94,10 @@ template <int CL> DC_DEV void cluster_wait() {
   if constexpr (CL > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+template <int CL> DC_DEV void cluster_arrive_relaxed() {
+  if constexpr (CL > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+
 template <int CL> DC_DEV float2* row_of(float2* sm, int owner) {
   if constexpr (CL > 1) return cg::this_cluster().map_shared_rank(sm, owner);
   else return sm;
@@ -77,7 +105,7 @@ template <int CL> DC_DEV float2* row_of(float2* sm, int owner) {
 
 // One 4096-point row per CTA; clusters of L1 CTAs (16 at L = 65536, beyond
 // the portable 8).  Register caps give 3 resident CTAs per SM for the
-// spectrum and apply kernels, 2 for the full correction (phase evaluation).
+// spectrum kernel, 2 for the full correction (phase evaluation).
 constexpr int kRowsPerCta = 1;
 
 template <int LOG2L1, int OP>
@@ -102,21 +130,7 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
   float2 v[16];
 
   // ---------------------------------------------------------- input side
-  if constexpr (OP == FUSED_APPLY) {
-    // spectrum row k1 -> A, phase row k1 -> B (two 32 KiB bulk copies)
-    __shared__ __align__(8) unsigned long long bar;
-    if (t == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    if (t == 0) {
-      mbar_expect_tx(&bar, 2 * kRowN * sizeof(float2));
-      bulk_g2s(bufA, I.src + (size_t)k1 * kRowN, kRowN * sizeof(float2), &bar);
-      bulk_g2s(bufB, I.ptab + (size_t)k1 * kRowN, kRowN * sizeof(float2), &bar);
-    }
-    mbar_wait_bounded(&bar, 0, a.err);   // on a timeout: flag raised, keep going
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = cmul(bufA[j + 256 * r], bufB[j + 256 * r]);
-    __syncthreads();                     // the row FFT overwrites A and B
-  } else if constexpr (LOG2L1 == 0) {
+  if constexpr (LOG2L1 == 0) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int n = j + 256 * r;
@@ -147,13 +161,13 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
   // ---------------------------------------------------------------- rows
   // FULL/SPEC: the input sits in A (read above), so the forward row starts in
   // B; its last exchange is in A, so the inverse row starts in B again.
-  if constexpr (OP == FUSED_FULL || OP == FUSED_SPEC) row4096<-1>(v, bufB, bufA, j, a.tw);
+  row4096<-1>(v, bufB, bufA, j, a.tw);
   if constexpr (OP == FUSED_SPEC) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) I.dst[(size_t)k1 * kRowN + j + 256 * r] = v[r];
     return;
   }
-  if constexpr (OP == FUSED_FULL) {
+  {
     const float invL = 1.0f / (float)(1 << LOG2L);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -161,14 +175,10 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
       v[r] = cscale(cmul(v[r], w), invL);
     }
   }
-  if constexpr (OP == FUSED_FULL) {
-    // B was last read before the forward's second barrier; A (read by the
-    // forward's stage 3) is next written after the inverse's first barrier.
-    row4096<+1>(v, bufB, bufA, j, a.tw);       // result exchanged last through A
-  } else {
-    row4096<+1>(v, bufA, bufB, j, a.tw);       // result exchanged last through B
-  }
-  float2* out_buf = OP == FUSED_FULL ? bufB : bufA; // free: last read before a barrier
+  // B was last read before the forward's second barrier; A (read by the
+  // forward's stage 3) is next written after the inverse's first barrier.
+  row4096<+1>(v, bufB, bufA, j, a.tw);         // result exchanged last through A
+  float2* out_buf = bufB;                      // free: last read before a barrier
 
   // ------------------------------------------------------------ output side
   if constexpr (LOG2L1 == 0) {
@@ -193,7 +203,7 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
 #pragma unroll
     for (int r = 0; r < 16; ++r) out_buf[pad16(j + 256 * r)] = v[r];
     cluster_sync<CL>();
-    const int out_off = OP == FUSED_FULL ? kRowPitch : 0;   // buffer B or A of each row
+    const int out_off = kRowPitch;             // buffer B of each row
     for (int c = t; c < COLS; c += NT) {
       const int n2 = rank * COLS + c;
       float2 col[L1];
@@ -234,6 +244,117 @@ cudaError_t launch_one(const FusedArgs& a, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
+
+
+// Spectrum apply (FUSED_APPLY): one row k1 of the transform per CTA, one
+// cluster of L1 CTAs per transform.  The spectrum row arrives by one 32 KiB
+// bulk copy, the phase row by coalesced loads; after the inverse row FFT
+// each thread sends its 16 outputs X[n2 = j + 256 r] straight to the CTA
+// that owns column n2 (asynchronous remote stores counted on the owner's
+// receive mbarrier), so no CTA reads another's shared memory and the only
+// cluster barrier is the one that publishes the receive barriers at start.
+// The owner then applies W_L^(-n2 q) from the table and runs its columns.
+template <int LOG2L1>
+__global__ void __launch_bounds__(kRowThreads, 3) apply_kernel(FusedArgs a) {
+  constexpr int L1 = 1 << LOG2L1;
+  constexpr int COLS = kRowN / L1;              // columns owned by a CTA
+  constexpr int PER = COLS / kRowThreads;       // columns per thread
+  extern __shared__ __align__(128) float2 sm[];
+  float2* A = sm;                               // [kRowPitch] row buffer
+  float2* R = sm + kRowPitch;                   // [L1][COLS] received rows (L1 > 1)
+  __shared__ __align__(8) unsigned long long bar_in, bar_r;
+
+  const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const FftItem I = a.items[blockIdx.x >> LOG2L1];
+  const int j = threadIdx.x;
+  if (j == 0) {
+    mbar_init(&bar_in, 1);
+    if constexpr (L1 > 1) {
+      mbar_init(&bar_r, 1);
+      mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
+    }
+  }
+  __syncthreads();
+  cluster_arrive_relaxed<L1>();                 // receive barrier published
+  if (j == 0) {
+    mbar_expect_tx(&bar_in, kRowN * sizeof(float2));
+    bulk_g2s(A, I.src + (size_t)k1 * kRowN, kRowN * sizeof(float2), &bar_in);
+  }
+  float2 v[16];
+  const float2* prow = I.ptab + (size_t)k1 * kRowN;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = __ldg(prow + j + 256 * r);
+  mbar_wait_bounded(&bar_in, 0, a.err);         // on a timeout: flag raised, keep going
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = cmul(A[j + 256 * r], v[r]);
+  __syncthreads();                              // the row FFT overwrites A
+  row4096_1buf<+1>(v, A, j, a.tw);
+
+  if constexpr (L1 == 1) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int n = j + 256 * r;
+      if (n < I.n_out) __stcs(I.dst + n, v[r]);
+    }
+  } else {
+    cluster_wait<L1>();                         // every peer's bar_r is initialised
+    const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
+    const uint32_t b_loc = smem_addr(&bar_r);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int owner = r / PER;                // n2 = j + 256 r -> owner n2 / COLS
+      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));
+      st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
+    }
+    const float2* T = a.t4 + kT4Offset(L1);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int c = j + 256 * p;
+      const int n2 = k1 * COLS + c;
+      float2 w[L1];
+#pragma unroll
+      for (int q = 1; q < L1; ++q) w[q] = __ldg(T + q * kRowN + n2);
+      if (p == 0) mbar_wait_cluster_bounded(&bar_r, 0, a.err);
+      float2 col[L1];
+      col[0] = R[c];
+#pragma unroll
+      for (int q = 1; q < L1; ++q) col[q] = cmul(R[q * COLS + c], w[q]);
+      dft<L1, +1>(col);
+#pragma unroll
+      for (int n1 = 0; n1 < L1; ++n1) {
+        const int n = n2 + kRowN * n1;
+        if (n < I.n_out) __stcs(I.dst + n, col[n1]);
+      }
+    }
+  }
+}
+
+template <int LOG2L1>
+cudaError_t launch_apply(const FusedArgs& a, cudaStream_t s) {
+  constexpr int L1 = 1 << LOG2L1;
+  if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * (kRowPitch + (L1 > 1 ? kRowN : 0));
+  auto k = apply_kernel<LOG2L1>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (L1 > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n_items * L1));
+  cfg.blockDim = dim3(kRowThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = L1;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -303,7 +424,15 @@ cudaError_t launch_row_mid_4096(const RowArgs& a, cudaStream_t s) {
 cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
   switch (op) {
-    case FUSED_APPLY: return launch_op<FUSED_APPLY>(a, s);
+    case FUSED_APPLY:
+      switch (a.log2L) {
+        case 12: return launch_apply<0>(a, s);
+        case 13: return launch_apply<1>(a, s);
+        case 14: return launch_apply<2>(a, s);
+        case 15: return launch_apply<3>(a, s);
+        case 16: return launch_apply<4>(a, s);
+        default: return cudaErrorInvalidValue;
+      }
     case FUSED_FULL: return launch_op<FUSED_FULL>(a, s);
     case FUSED_SPEC: return launch_op<FUSED_SPEC>(a, s);
     default: return cudaErrorInvalidValue;

@@ -1,16 +1,19 @@
 // Cluster-fused FFT correction for 4096 <= L <= 65536 (Sec. II-B, Eq. 16).
 //
 // L = L1 x 4096 with L1 = L / 4096 <= 16 rows of 4096 points.  One thread
-// block cluster owns one transform: each CTA holds two rows (one when L1 = 1)
-// in shared memory, 256 threads per row run the three radix-16 Stockham
-// stages of a row with the data in registers, and the column DFTs of length
-// L1 read the other CTAs' rows through distributed shared memory.  The
+// block cluster owns one transform: each CTA holds one row in shared memory,
+// 256 threads per row run the three radix-16 Stockham stages of a row with
+// the data in registers, and the column DFTs of length L1 exchange data
+// with the other CTAs through distributed shared memory.  The
 // four-step intermediate never leaves the SMs, so a transform reads its input
 // once and writes its output once.
 //
 //   FUSED_APPLY : rows of a stored spectrum (bin k1 + L1 k2 at k1*4096 + k2)
 //                 times a phase table in the same layout (already scaled by
-//                 1/L) -> inverse rows -> W_L^(-n2 k1) -> inverse columns -> out
+//                 1/L) -> inverse rows -> pushed to the column owners with
+//                 asynchronous remote stores (st.async, completion counted
+//                 on the owner's mbarrier) -> W_L^(-n2 k1) -> inverse
+//                 columns -> out
 //   FUSED_FULL  : y (zero-padded) -> forward columns (DSMEM scatter) ->
 //                 forward rows -> exp(-i phi_k) / L -> inverse rows ->
 //                 inverse columns -> out (truncated to n_out)
@@ -29,7 +32,14 @@ struct FusedArgs {
   int log2L;              // 12..16
   const float2* tw;
   int* err;               // device error flag (bounded waits)
+  // FUSED_APPLY only: four-step twiddles W_L^(-q n2) = exp(+2 pi i q n2 / L)
+  // for q < L1, n2 < 4096, at t4 + kT4Offset(L1) + q * 4096 + n2.
+  const float2* t4;
 };
+
+// Four-step twiddle table for L1 = 2, 4, 8, 16 (rows of 4096), one block per L1.
+__host__ __device__ constexpr int kT4Offset(int l1) { return (l1 - 2) * 4096; }
+constexpr int kT4Size = 30 * 4096;
 
 // Launch; returns cudaErrorInvalidValue for L outside [4096, 65536].
 cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s);

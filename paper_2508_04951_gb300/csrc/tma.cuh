@@ -55,4 +55,42 @@ DC_DEV bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, int* err
   return false;
 }
 
+// ---------------------------------------------- distributed shared memory
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+DC_DEV uint32_t dsmem_map(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+
+// Asynchronous 8-byte store into a peer's shared memory; its arrival is
+// counted (8 bytes of transaction) on the peer's mbarrier `rbar`.
+DC_DEV void st_async_c64(uint32_t raddr, float2 v, uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+          raddr),
+      "f"(v.x), "f"(v.y), "r"(rbar)
+      : "memory");
+}
+
+// Cluster-scope acquire wait, for barriers completed by peers' st.async.
+DC_DEV bool mbar_try_wait_cluster(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+DC_DEV bool mbar_wait_cluster_bounded(unsigned long long* bar, uint32_t parity, int* err) {
+  for (int i = 0; i < kMbarPollLimit; ++i)
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+  if (err) atomicExch(err, 1);
+  for (int i = 0; i < kMbarPollLimit; ++i)
+    if (mbar_try_wait_cluster(bar, parity)) return false;
+  return false;
+}
+
 }  // namespace dc

@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "fused.cuh"
 
 namespace dc {
 
@@ -22,6 +23,20 @@ inline void fill_twiddles(float2* tw) {
   for (int r = 1; r < 16; ++r) {
     for (int k = 0; k < 16; ++k) tw[kTwS2 + (r - 1) * 16 + k] = w((r * k) % 256, 256.0);
     for (int j = 0; j < 256; ++j) tw[kTwS3 + (r - 1) * 256 + j] = w((r * j) % 4096, 4096.0);
+  }
+}
+
+// Four-step twiddles of the spectrum-apply kernel (layout in fused.cuh):
+// exp(+2 pi i m / L) with m = q n2 mod L, in double, rounded once.
+inline void fill_four_step(float2* t4) {
+  const double pi = 3.14159265358979323846;
+  for (int l1 = 2; l1 <= 16; l1 *= 2) {
+    const long long L = 4096LL * l1;
+    for (int q = 0; q < l1; ++q)
+      for (int n2 = 0; n2 < 4096; ++n2) {
+        const double a = 2.0 * pi * (double)(((long long)q * n2) % L) / (double)L;
+        t4[kT4Offset(l1) + q * 4096 + n2] = make_float2((float)std::cos(a), (float)std::sin(a));
+      }
   }
 }
 

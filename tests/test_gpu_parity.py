@@ -233,7 +233,11 @@ def test_correct_batch_exact_mode(dcg, ctx):
         assert rel(out[it["out_off"]:it["out_off"] + it["n_out"]], ref) <= TOL
 
 
-@pytest.mark.parametrize("n,n_v,n_tec", [(3000, 5, 3), (4096, 3, 2), (65536, 4, 3), (70000, 2, 2)])
+@pytest.mark.parametrize("n,n_v,n_tec", [
+    (3000, 5, 3), (4096, 3, 2),            # L = 4096: one CTA per transform
+    (5000, 3, 2), (12000, 2, 3), (30000, 2, 2),   # L = 8192, 16384, 32768: clusters of 2, 4, 8
+    (65536, 4, 3),                          # L = 65536: clusters of 16
+    (70000, 2, 2)])                         # L = 131072: three-pass path
 def test_correct_bank_matches_oracle(dcg, ctx, n, n_v, n_tec):
     import torch
     x = noise(n, salt=n % 13)
