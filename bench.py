@@ -48,10 +48,10 @@ METRIC = "corrected Msamples/s and p50/p99 pulse latency vs plain path at stated
 UNIT = "Msamples/s"
 ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
 # DRAM bytes (read + write) per launch of the kernel at the full workload, from
-# one ncu capture (profiles/fused_apply_doppler_bank_32v.md: 232.6 MB for the
+# one ncu capture (profiles/fused_apply_doppler_bank_32v.md: 232.9 MB for the
 # reduced 32-range-rate launch, scaled by the 8x units of the full launch).
 # Cleared whenever the kernel changes after the capture.
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": None}
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 8 * 232.944e6}
 
 
 def load_peaks() -> tuple[float, str]:
@@ -125,6 +125,34 @@ def oracle_bank_sample(x, v, tec, cfg, n_v_sample: int):
     out = oracle.correct_bank(x.astype(np.complex128), cfg.fs, cfg.fc, v[:n_v_sample], tec)
     dt = time.perf_counter() - t0
     return out, dt
+
+
+def _pool_warm(_):
+    import oracle  # noqa: F401  (import cost kept out of the timed map)
+    return os.getpid()
+
+
+def _pool_bank_chunk(job):
+    import oracle
+    x, fs, fc, v, tec = job
+    oracle.correct_bank(x, fs, fc, v, tec)
+    return len(v)
+
+
+def oracle_bank_allcores(x, v, tec, cfg, per_core: int):
+    """The same oracle, one process per host core (spawned, so safe after CUDA
+    is initialised), each on its own per_core range rates x all TECs.
+    Returns (Msamples/s, cores, wall seconds of the timed map)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    x128 = x.astype(np.complex128)
+    jobs = [(x128, cfg.fs, cfg.fc, np.roll(v, -per_core * k)[:per_core], tec) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_pool_warm, range(cores), chunksize=1)
+        t0 = time.perf_counter()
+        pool.map(_pool_bank_chunk, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    return cores * per_core * len(tec) * cfg.n / wall / 1e6, cores, wall
 
 
 # ------------------------------------------------------------- reference arm
@@ -314,10 +342,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         ref, dt = oracle_bank_sample(x, v, tec, cfg, n_vs)
         got = oh.numpy().reshape(cfg.n_v, cfg.n_tec, cfg.n)[:n_vs].astype(np.complex128)
         errs = np.linalg.norm(got - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
-        result["cpu_baseline"] = {"value": n_vs * cfg.n_tec * cfg.n / dt / 1e6, "unit": UNIT,
-                                  "cores": 1, "kind": "oracle",
+        single = n_vs * cfg.n_tec * cfg.n / dt / 1e6
+        result["cpu_baseline"] = {"value": single, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": f"first {n_vs} range rates x {cfg.n_tec} TECs x {cfg.n} "
                                             f"samples of the bank, numpy FP64 single thread, {dt:.1f} s"}
+        if args.cpu_all_cores:
+            rate, cores, wall = oracle_bank_allcores(x, v, tec, cfg, args.cpu_per_core_v)
+            result["cpu_baseline_all_cores"] = {
+                "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{cores} spawned processes x {args.cpu_per_core_v} range rates x "
+                          f"{cfg.n_tec} TECs x {cfg.n} samples, {wall:.1f} s"}
         result["error"] = {"rel_l2_max": float(errs.max()), "rel_l2_median": float(np.median(errs)),
                            "pairs_checked": int(errs.size), "tolerance": 1e-5}
     if rank == 0:
@@ -376,16 +410,21 @@ def run_split(args) -> None:
     samples = V * P * n
     t = sum(ms) / len(ms)
     # error on sampled outputs vs the FP64 oracle (row by row)
+    # (every range rate x 8 pulses x 32 sampled output rows; the oracle's
+    # time on that subset is its per-sample CPU rate)
     import oracle
     rng = np.random.default_rng(4)
-    rows = np.sort(rng.choice(n, 64, replace=False))
-    Y = yd.view(V, P, n)
+    rows = np.sort(rng.choice(n, 32, replace=False))
+    pulses = np.linspace(0, P - 1, 8).astype(int)
+    Yh = yd.view(V, P, n)[:, pulses].cpu().numpy().astype(np.complex128)[:, :, rows]
     errs = []
-    for i in (0, V // 2, V - 1):
-        for p in (0, P // 2, P - 1):
+    t_or = 0.0
+    for i in range(V):
+        for pj, p in enumerate(pulses):
+            t0 = time.perf_counter()
             ref = oracle.resample_exact_rows(X[p].astype(np.complex128), oracle.alpha(v[i]), rows)
-            got = Y[i, p].cpu().numpy().astype(np.complex128)[rows]
-            errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+            t_or += time.perf_counter() - t0
+            errs.append(float(np.linalg.norm(Yh[i, pj] - ref) / np.linalg.norm(ref)))
     # FP32 CUDA-core path, one step
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -415,8 +454,12 @@ def run_split(args) -> None:
                      "frac_algorithmic": algo / (k_ms / 1e3) / 1e12 / peak,
                      "kernel_ms": k_ms, "phases_ms_per_step": {k: vv[2] / args.steps for k, vv in prof.items()}},
         "fp32_cuda_core": {"ms_per_step": fp32_ms, "value": samples / (fp32_ms / 1e3) / 1e6},
-        "error": {"rel_l2_max": max(errs), "pairs_checked": len(errs), "rows_per_pair": len(rows),
-                  "tolerance": 1e-3},
+        "error": {"rel_l2_max": max(errs), "rel_l2_median": float(np.median(errs)),
+                  "pairs_checked": len(errs), "rows_per_pair": len(rows), "tolerance": 1e-3},
+        "cpu_baseline": {"value": len(errs) * len(rows) / t_or / 1e6, "unit": UNIT, "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{V} range rates x {len(pulses)} pulses x {len(rows)} output rows "
+                                   f"(each a {n}-term FP64 sum), {t_or:.1f} s"},
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -502,9 +545,13 @@ def run_batch(args) -> None:
     import oracle
     out = od.cpu().numpy()
     errs = []
+    t_or, s_or = 0.0, 0
     for i in rng.choice(cfg.n_pulses, 12, replace=False):
         n = int(lens[i])
+        t0 = time.perf_counter()
         ref = oracle.correct(x[offs[i]:offs[i] + n].astype(np.complex128), cfg.fs, cfg.fc, v[i], tec[i])
+        t_or += time.perf_counter() - t0
+        s_or += n
         got = out[offs[i]:offs[i] + n].astype(np.complex128)
         errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
     line = {
@@ -522,9 +569,113 @@ def run_batch(args) -> None:
                        "p50_ms": float(np.percentile(plain, 50)), "p99_ms": float(np.percentile(plain, 99)),
                        "pulses_timed": len(plain)},
         "error": {"rel_l2_max": max(errs), "pulses_checked": len(errs), "tolerance": 1e-5},
+        "cpu_baseline": {"value": s_or / t_or / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the {len(errs)} checked pulses ({s_or} samples), {t_or:.1f} s"},
     }
     print(json.dumps(line), flush=True)
     plan.close()
+    ctx.close()
+
+
+# ------------------------------------------------------ plain single pulse
+
+def run_plain(args) -> None:
+    """One LFM pulse (N = 4096, fs = 10 MHz, B = 5 MHz, fc = 1 GHz, v_r = +7.5
+    km/s, TEC = 50 TECU) corrected end to end, windowed and exact-sinc: per
+    mode a captured plan (one graph launch) replayed --replays times, each
+    replay timed by CUDA events on the device and by the host from submission
+    to completion, against direct entry-point calls (doppler_resample +
+    iono_correct) and the FP64 oracle on one host core."""
+    import torch
+    import paper_2508_04951_gb300 as dcg
+
+    dcg.build.build()
+    dcg.load()
+    import oracle
+    cfg = synth.PlainPulse()
+    n = cfg.n
+    x = cfg.pulse().astype(np.complex64)
+    ctx = dcg.Context(0)
+    stream = torch.cuda.current_stream()
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    od = torch.empty_like(xd)
+    items = np.zeros(1, dtype=dcg.ITEM_DTYPE)
+    items[0] = (0, n, 0, n, cfg.fs, cfg.fc, cfg.v_r, cfg.tec)
+    R = args.replays
+    modes = {}
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    for name, mode in (("windowed", dcg.DC_WINDOWED), ("exact", dcg.DC_EXACT_FP32)):
+        plan = dcg.dc_plan_batch(ctx, xd, od, items, mode=mode)
+        for _ in range(max(3, args.warmup)):
+            plan.execute()
+        dcg.dc_check(ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(R)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            plan.execute()
+            b.record(stream)
+        torch.cuda.synchronize()
+        dev_ms = [a.elapsed_time(b) for a, b in ev]
+        host_ms = []
+        for _ in range(min(R, 2000)):
+            t0 = time.perf_counter()
+            plan.execute()
+            torch.cuda.synchronize()
+            host_ms.append(1e3 * (time.perf_counter() - t0))
+        got = od.cpu().numpy().astype(np.complex128)
+        launches = plan.launches
+        plan.close()
+        # direct calls: two entry points per pulse, no graph
+        pe = []
+        for k in range(min(R, 2000) + 8):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dcg.doppler_resample(ctx, xd, yd, cfg.fs, cfg.fc, cfg.v_r, mode=mode)
+            dcg.iono_correct(ctx, yd, od, cfg.fs, cfg.fc, cfg.tec)
+            b.record(stream)
+            if k >= 8:
+                pe.append((a, b))
+        torch.cuda.synchronize()
+        direct = [a.elapsed_time(b) for a, b in pe]
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            ref = oracle.correct(x.astype(np.complex128), cfg.fs, cfg.fc, cfg.v_r, cfg.tec, mode=name)
+            reps += 1
+            if time.perf_counter() - t0 > 2.0:
+                break
+        t_or = (time.perf_counter() - t0) / reps
+        modes[name] = {
+            "value": n / (float(np.median(dev_ms)) / 1e3) / 1e6, "unit": UNIT,
+            "device_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
+            "host_ms": {"p50": float(np.percentile(host_ms, 50)), "p99": float(np.percentile(host_ms, 99))},
+            "graph_launches_per_pulse": launches, "replays": R,
+            "plain_path": {"what": "doppler_resample + iono_correct calls, device time",
+                           "p50_ms": float(np.percentile(direct, 50)),
+                           "p99_ms": float(np.percentile(direct, 99)),
+                           "value": n / (float(np.median(direct)) / 1e3) / 1e6},
+            "error": {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), "tolerance": 1e-5},
+            "cpu_baseline": {"value": n / t_or / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the pulse, {reps} repetitions, {1e3 * t_or:.2f} ms each"},
+        }
+    clk = clocks.stop()
+    w = modes["windowed"]
+    line = {
+        "metric": METRIC, "value": w["value"], "unit": UNIT, "n_gpus": 1, "steps": R,
+        "warmup": max(3, args.warmup), "ms_per_step": w["device_ms"]["p50"], "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plain_pulse", "n": n, "fs_hz": cfg.fs, "bandwidth_hz": cfg.bandwidth,
+                   "fc_hz": cfg.fc, "v_r": cfg.v_r, "tec_tecu": cfg.tec, "signal": "LFM",
+                   "l2": "32 KiB pulse: L2-resident by design (latency workload)"},
+        "latency_ms": {"p50": w["device_ms"]["p50"], "p99": w["device_ms"]["p99"]},
+        "clocks": clk, "modes": modes,
+    }
+    print(json.dumps(line), flush=True)
     ctx.close()
 
 
@@ -570,6 +721,10 @@ def run_serve(args) -> None:
             n = int(lens[i])
             ids[i] = srv.submit(pool[src[i]][:n], ring[i % R][:n], cfg.fs, cfg.fc, v[i], tec[i])
 
+    # results of a few requests are kept (their ring slot is reused later)
+    # and checked against the oracle after the run
+    check = set(int(i) for i in rng.choice(nreq, min(args.serve_check, nreq), replace=False))
+    kept = {}
     th = threading.Thread(target=submitter)
     t_start = time.perf_counter()
     th.start()
@@ -577,6 +732,8 @@ def run_serve(args) -> None:
         while ids[i] is None:
             time.sleep(20e-6)
         srv.wait(ids[i])
+        if i in check:
+            kept[i] = ring[i % R][:int(lens[i])].copy()
         with cond:
             done_upto[0] = i + 1
             cond.notify()
@@ -605,6 +762,15 @@ def run_serve(args) -> None:
         lat.append(time.perf_counter() - t0 - arrivals[i])
     serial_wall = time.perf_counter() - t0
     ctx.close()
+    import oracle
+    errs, t_or, s_or = [], 0.0, 0
+    for i in sorted(kept):
+        n = int(lens[i])
+        t1 = time.perf_counter()
+        ref = oracle.correct(pool[src[i]][:n].astype(np.complex128), cfg.fs, cfg.fc, v[i], tec[i])
+        t_or += time.perf_counter() - t1
+        s_or += n
+        errs.append(float(np.linalg.norm(kept[i].astype(np.complex128) - ref) / np.linalg.norm(ref)))
     line = {
         "metric": METRIC, "value": st["msamples_per_s"], "unit": UNIT, "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -620,6 +786,11 @@ def run_serve(args) -> None:
                        "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                        "p99_ms": 1e3 * float(np.percentile(lat, 99))},
     }
+    if errs:
+        line["error"] = {"rel_l2_max": max(errs), "requests_checked": len(errs), "tolerance": 1e-5,
+                         "sample": "random requests of the served stream, results copied at completion"}
+        line["cpu_baseline"] = {"value": s_or / t_or / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the {len(errs)} checked requests ({s_or} samples), {t_or:.1f} s"}
     print(json.dumps(line), flush=True)
 
 
@@ -634,9 +805,17 @@ def main() -> None:
     ap.add_argument("--cpu-sample-v", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-v", type=int, default=None, help="fewer range rates (small profiling case)")
-    ap.add_argument("--workload", choices=["bank", "split", "batch", "serve"], default="bank",
-                    help="bank: the Doppler-bank headline line; split: the exact-sinc tensor-core "
-                         "GEMM; batch: the uneven batch; serve: the Poisson request stream")
+    ap.add_argument("--workload", choices=["bank", "plain", "split", "batch", "serve"], default="bank",
+                    help="bank: the Doppler-bank headline line; plain: one LFM pulse, graph "
+                         "replays; split: the exact-sinc tensor-core GEMM; batch: the uneven "
+                         "batch; serve: the Poisson request stream")
+    ap.add_argument("--replays", type=int, default=10000, help="plain: graph replays per mode")
+    ap.add_argument("--cpu-all-cores", action=argparse.BooleanOptionalAction, default=True,
+                    help="bank: also time the oracle on every host core (spawned processes)")
+    ap.add_argument("--cpu-per-core-v", type=int, default=4,
+                    help="bank: range rates per process in the all-core oracle sample")
+    ap.add_argument("--serve-check", type=int, default=12,
+                    help="serve: requests whose results are checked against the oracle")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--serial-seconds", type=float, default=1.0, help="serve: seconds for the serial server")
     ap.add_argument("--slots", type=int, default=3, help="serve: batches in flight")
@@ -649,6 +828,9 @@ def main() -> None:
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "plain":
+        run_plain(args)
         return
     if args.workload == "split":
         run_split(args)

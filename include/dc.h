@@ -202,7 +202,7 @@ DC_API dc_status correct_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n, con
  * contraction Y_a = X_a S_a^T, S_a[j][i] = sinc(alpha_a j - i)).
  * x_dev: pulses [n_alpha][n_pulses][n] with x_alpha_stride samples between
  *        consecutive alpha groups (0 = every alpha uses the same pulses);
- * v_r:   host [n_alpha];
+ * v_r:   host [n_alpha], 1 <= n_alpha <= 65535;
  * y_dev: [n_alpha][n_pulses][n_out].
  * mode:  DC_EXACT_FP32 (CUDA cores), DC_EXACT_BF16X3 or DC_EXACT_FP16X3
  *        (tcgen05 tensor cores with hi/lo split operands, FP32 accumulation). */

@@ -908,6 +908,7 @@ extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long 
   std::lock_guard<std::recursive_mutex> g(c->mu);
   if (!x || !y || !v_r || n_alpha < 1 || n_pulses < 1)
     return fail(c, DC_EINVAL, "bad exact-batch arguments");
+  if (n_alpha > 65535) return fail(c, DC_EINVAL, "n_alpha %d above 65535", n_alpha);
   if (n_out == 0) n_out = n;
   dc_status st;
   for (int i = 0; i < n_alpha; ++i)

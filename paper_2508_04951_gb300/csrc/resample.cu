@@ -406,8 +406,70 @@ __global__ void __launch_bounds__(256) exact_fp32_kernel(ExArgs a) {
   }
 }
 
+// The same sum for a few pulses (a matrix-vector product: one pulse per
+// call of the single-pulse entry points): one warp per output sample, lanes
+// striding the input, the weight computed once per (n, m) and applied to
+// every pulse, lanes combined by a fixed shuffle tree (deterministic).
+template <int P>
+__global__ void __launch_bounds__(256) exact_gemv_kernel(ExArgs a) {
+  const ExItem& I = a.items[blockIdx.y];
+  const int n = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (n >= a.n_out) return;
+  const int np = a.n_pulses;
+  int fl;
+  float e;
+  rs_delay(I.dl_hi, I.dl_lo, (float)n, fl, e);
+  const int mn = n + fl;
+  if (e == 0.f) {                                  // alpha n on a sample: copy it
+    if (lane < np) {
+      const bool in = mn >= 0 && mn < a.n_in;
+      I.y[(size_t)lane * a.n_out + n] = in ? __ldg(I.x + (size_t)lane * a.n_in + mn)
+                                           : make_float2(0.f, 0.f);
+    }
+    return;
+  }
+  const float s = sinpif(e) * kInvPi;
+  const float sg = (mn & 1) ? -s : s;
+  float2 acc[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = make_float2(0.f, 0.f);
+  for (int m = lane; m < a.n_in; m += 32) {
+    const float den = (float)(mn - m) + e;
+    const float w = __fdividef((m & 1) ? -sg : sg, den);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      if (p < np) {
+        const float2 x = __ldg(I.x + (size_t)p * a.n_in + m);
+        acc[p].x = fmaf(x.x, w, acc[p].x);
+        acc[p].y = fmaf(x.y, w, acc[p].y);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[p].x += __shfl_xor_sync(0xffffffffu, acc[p].x, o);
+      acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, o);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if (p < np) I.y[(size_t)p * a.n_out + n] = acc[p];
+  }
+}
+
 cudaError_t launch_exact_fp32(const ExArgs& a, int n_alpha, cudaStream_t s) {
   if (n_alpha <= 0 || a.n_out <= 0 || a.n_pulses <= 0) return cudaSuccess;
+  if (a.n_pulses <= 8) {
+    dim3 grid((a.n_out + 7) / 8, n_alpha);
+    if (a.n_pulses == 1) exact_gemv_kernel<1><<<grid, 256, 0, s>>>(a);
+    else if (a.n_pulses <= 2) exact_gemv_kernel<2><<<grid, 256, 0, s>>>(a);
+    else if (a.n_pulses <= 4) exact_gemv_kernel<4><<<grid, 256, 0, s>>>(a);
+    else exact_gemv_kernel<8><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   dim3 grid((a.n_out + kExBN - 1) / kExBN, (a.n_pulses + kExBP - 1) / kExBP, n_alpha);
   exact_fp32_kernel<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();

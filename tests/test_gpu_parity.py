@@ -116,6 +116,24 @@ def test_exact_fp32_matches_oracle(dcg, ctx, n, n_out, v):
     assert rel(host(yd), ref) <= TOL
 
 
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8, 9])
+def test_exact_fp32_few_pulses(dcg, ctx, P):
+    # 1..8 pulses per range rate take the warp-per-output kernel, 9 the tiled one;
+    # alpha = 1 exactly (v = 0) exercises the copy branch of every output
+    import torch
+    n, n_out = 777, 801
+    X = np.stack([noise(n, salt=200 + p) for p in range(P)])
+    v = np.array([-6000.0, 0.0, 3500.0])
+    yd = torch.empty(len(v) * P * n_out, dtype=torch.complex64, device="cuda:0")
+    dcg.resample_exact_batch(ctx, to_dev(X.reshape(-1)), n, P, v, yd, n_out=n_out,
+                             mode=dcg.DC_EXACT_FP32)
+    Y = host(yd).reshape(len(v), P, n_out)
+    for i in range(len(v)):
+        ref = oracle.resample_exact(X.astype(np.complex128), oracle.alpha(v[i]), n_out)
+        for p in range(P):
+            assert rel(Y[i, p], ref[p]) <= TOL, (i, p)
+
+
 def test_exact_fp32_batch_many_alpha(dcg, ctx):
     import torch
     n, P, V = 1024, 40, 5
