@@ -357,7 +357,7 @@ dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2*
     dc_status st = upload(c, it, item_at, s, &dev);
     if (st) return st;
     item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
-    FusedArgs a{dev, (int)it.size(), log2L, c->tw, c->err};
+    FusedArgs a{dev, (int)it.size(), log2L, c->tw, c->err, c->t4};
     long long outs = 0;
     for (auto& f : it) outs += f.n_out;
     Phase ph(c, PH_FUSED_FULL, s, outs);
@@ -821,7 +821,7 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   if (fused) {
     if ((st = upload(c, sp, item_at, s, &dev))) return st;
     item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
-    FusedArgs a{dev, n_v, log2L, c->tw, c->err};
+    FusedArgs a{dev, n_v, log2L, c->tw, c->err, c->t4};
     Phase ph(c, PH_FUSED_SPEC, s, (long long)n_v * n_out);
     if ((e = launch_fused(FUSED_SPEC, a, s)) != cudaSuccess) return cuda_fail(c, e, "spec launch");
   } else if (!four) {

@@ -155,6 +155,32 @@ template <int R, int DIR> DC_DEV void dft(float2 (&v)[R]) {
   }
 }
 
+// v[q] *= w^q for q = 1 .. N-1 (N = 2, 4, 8, 16) from correctly rounded
+// b[0] = w, b[1] = w^2, b[2] = w^4, b[3] = w^8 (entries past log2 N unused):
+// w^q is the product of the bases of q's set bits, so every factor carries
+// at most three roundings beyond the table's own.
+template <int N> DC_DEV void apply_powers(float2 (&v)[N], const float2 (&b)[4]) {
+  static_assert(N == 2 || N == 4 || N == 8 || N == 16, "N must be 2, 4, 8 or 16");
+  float2 p[N];
+  p[1] = b[0];
+  if constexpr (N > 2) {
+    p[2] = b[1];
+    p[3] = cmul(b[1], b[0]);
+  }
+  if constexpr (N > 4) {
+    p[4] = b[2];
+#pragma unroll
+    for (int q = 1; q < 4; ++q) p[4 + q] = cmul(b[2], p[q]);
+  }
+  if constexpr (N > 8) {
+    p[8] = b[3];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) p[8 + q] = cmul(b[3], p[q]);
+  }
+#pragma unroll
+  for (int q = 1; q < N; ++q) v[q] = cmul(v[q], p[q]);
+}
+
 // --------------------------------------------------------------- twiddles
 // One device table of roots of unity, filled once per context in FP64 on the
 // host and rounded to float (fill_twiddles in twiddle_host.h):

@@ -16,17 +16,26 @@ constexpr int kRowPitch = kRowN + kRowN / 16;
 
 DC_DEV int pad16(int p) { return p + (p >> 4); }
 
-// Stage twiddles of a 4096-point row from the precomputed tables:
-// stage 2 multiplies v[r] by W256^(r k), k = j mod 16; stage 3 by W4096^(r j).
+// Stage twiddles of a 4096-point row from the precomputed tables: stage 2
+// multiplies v[r] by W256^(r k), k = j mod 16; stage 3 by W4096^(r j).  Only
+// the table rows r = 1, 2, 4, 8 are read (coalesced across the warp); the
+// other powers are their products (apply_powers).  The bases are loaded
+// ahead of the CTA barrier that precedes their use.
 template <int DIR>
-DC_DEV void twiddle_stage2(float2 (&v)[16], const float2* __restrict__ tw, int k) {
-#pragma unroll
-  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], conj_if<DIR>(__ldg(tw + kTwS2 + (r - 1) * 16 + k)));
+DC_DEV void stage2_bases(float2 (&b)[4], const float2* __restrict__ tw, int k) {
+  const float2* t = tw + kTwS2 + k;             // row r at (r - 1) * 16
+  b[0] = conj_if<DIR>(__ldg(t));
+  b[1] = conj_if<DIR>(__ldg(t + 16));
+  b[2] = conj_if<DIR>(__ldg(t + 48));
+  b[3] = conj_if<DIR>(__ldg(t + 112));
 }
 template <int DIR>
-DC_DEV void twiddle_stage3(float2 (&v)[16], const float2* __restrict__ tw, int j) {
-#pragma unroll
-  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], conj_if<DIR>(__ldg(tw + kTwS3 + (r - 1) * 256 + j)));
+DC_DEV void stage3_bases(float2 (&b)[4], const float2* __restrict__ tw, int j) {
+  const float2* t = tw + kTwS3 + j;             // row r at (r - 1) * 256
+  b[0] = conj_if<DIR>(__ldg(t));
+  b[1] = conj_if<DIR>(__ldg(t + 256));
+  b[2] = conj_if<DIR>(__ldg(t + 768));
+  b[3] = conj_if<DIR>(__ldg(t + 1792));
 }
 
 // One 4096-point row, thread j of 256.  In: v[r] = x[j + 256 r].
@@ -38,21 +47,24 @@ DC_DEV void twiddle_stage3(float2 (&v)[16], const float2* __restrict__ tw, int j
 template <int DIR>
 DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
                     const float2* __restrict__ tw) {
+  float2 w[4];
   dft16<DIR>(v);                                           // Ns = 1
 #pragma unroll
   for (int r = 0; r < 16; ++r) b1[pad16(16 * j + r)] = v[r];
+  stage2_bases<DIR>(w, tw, j & 15);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = b1[pad16(j + 256 * r)];
-  twiddle_stage2<DIR>(v, tw, j & 15);                      // Ns = 16: W256^(r k)
+  apply_powers<16>(v, w);                                  // Ns = 16: W256^(r k)
   dft16<DIR>(v);
   const int base = (j >> 4) * 256 + (j & 15);
 #pragma unroll
   for (int r = 0; r < 16; ++r) b2[pad16(base + 16 * r)] = v[r];
+  stage3_bases<DIR>(w, tw, j);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = b2[pad16(j + 256 * r)];
-  twiddle_stage3<DIR>(v, tw, j);                           // Ns = 256: W4096^(r j)
+  apply_powers<16>(v, w);                                  // Ns = 256: W4096^(r j)
   dft16<DIR>(v);
 }
 
@@ -61,22 +73,25 @@ DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
 // reading b.
 template <int DIR>
 DC_DEV void row4096_1buf(float2 (&v)[16], float2* b, int j, const float2* __restrict__ tw) {
+  float2 w[4];
   dft16<DIR>(v);
 #pragma unroll
   for (int r = 0; r < 16; ++r) b[pad16(16 * j + r)] = v[r];
+  stage2_bases<DIR>(w, tw, j & 15);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
-  twiddle_stage2<DIR>(v, tw, j & 15);
+  apply_powers<16>(v, w);
   dft16<DIR>(v);
   const int base = (j >> 4) * 256 + (j & 15);
+  stage3_bases<DIR>(w, tw, j);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) b[pad16(base + 16 * r)] = v[r];
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
-  twiddle_stage3<DIR>(v, tw, j);
+  apply_powers<16>(v, w);
   dft16<DIR>(v);
 }
 
@@ -137,8 +152,8 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
       v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
     }
   } else {
-    // forward columns (length L1) of this CTA's column range, scattered to the
-    // rows' owners, times W_L^(n2 k1)
+    // forward columns (length L1) of this CTA's column range, times
+    // W_L^(n2 k1), scattered to the rows' owners
     for (int c = t; c < COLS; c += NT) {
       const int n2 = rank * COLS + c;
       float2 col[L1];
@@ -148,8 +163,10 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
         col[n1] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
       }
       dft<L1, -1>(col);
+      float2 w[4];                             // W_L^(2^b n2), conjugates of the table rows
 #pragma unroll
-      for (int q = 1; q < L1; ++q) col[q] = cmul(col[q], tw_big<-1>(a.tw, (uint32_t)(n2 * q), LOG2L));
+      for (int b = 0; b < LOG2L1; ++b) w[b] = conj_if<+1>(__ldg(a.t4 + kT4Offset(L1) + b * kRowN + n2));
+      apply_powers<L1>(col, w);
 #pragma unroll
       for (int q = 0; q < L1; ++q) row_of<CL>(sm, q / ROWS)[(2 * (q % ROWS)) * kRowPitch + pad16(n2)] = col[q];
     }
@@ -225,6 +242,7 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
 template <int LOG2L1, int OP>
 cudaError_t launch_one(const FusedArgs& a, cudaStream_t s) {
   constexpr int L1 = 1 << LOG2L1;
+  if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
   constexpr int ROWS = L1 >= kRowsPerCta ? kRowsPerCta : 1;
   constexpr int CL = L1 / ROWS;
   constexpr int NT = ROWS * kRowThreads;
@@ -317,14 +335,14 @@ __global__ void __launch_bounds__(kRowThreads, 3) apply_kernel(FusedArgs a) {
     for (int p = 0; p < PER; ++p) {
       const int c = j + 256 * p;
       const int n2 = k1 * COLS + c;
-      float2 w[L1];
+      float2 w[4];
 #pragma unroll
-      for (int q = 1; q < L1; ++q) w[q] = __ldg(T + q * kRowN + n2);
+      for (int b = 0; b < LOG2L1; ++b) w[b] = __ldg(T + b * kRowN + n2);   // W_L^(-2^b n2)
       if (p == 0) mbar_wait_cluster_bounded(&bar_r, 0, a.err);
       float2 col[L1];
-      col[0] = R[c];
 #pragma unroll
-      for (int q = 1; q < L1; ++q) col[q] = cmul(R[q * COLS + c], w[q]);
+      for (int q = 0; q < L1; ++q) col[q] = R[q * COLS + c];
+      apply_powers<L1>(col, w);
       dft<L1, +1>(col);
 #pragma unroll
       for (int n1 = 0; n1 < L1; ++n1) {

@@ -32,14 +32,18 @@ struct FusedArgs {
   int log2L;              // 12..16
   const float2* tw;
   int* err;               // device error flag (bounded waits)
-  // FUSED_APPLY only: four-step twiddles W_L^(-q n2) = exp(+2 pi i q n2 / L)
-  // for q < L1, n2 < 4096, at t4 + kT4Offset(L1) + q * 4096 + n2.
+  // Four-step twiddles W_L^(-q n2) = exp(+2 pi i q n2 / L) (L1 > 1)
+  // for q = 2^b < L1, n2 < 4096, at t4 + kT4Offset(L1) + b * 4096 + n2
+  // (the other q are products of these rows).
   const float2* t4;
 };
 
-// Four-step twiddle table for L1 = 2, 4, 8, 16 (rows of 4096), one block per L1.
-__host__ __device__ constexpr int kT4Offset(int l1) { return (l1 - 2) * 4096; }
-constexpr int kT4Size = 30 * 4096;
+// Four-step twiddle rows for L1 = 2, 4, 8, 16: log2(L1) rows of 4096 per L1.
+__host__ __device__ constexpr int kT4Log2(int l1) { return l1 >= 16 ? 4 : l1 >= 8 ? 3 : l1 >= 4 ? 2 : 1; }
+__host__ __device__ constexpr int kT4Offset(int l1) {
+  return kT4Log2(l1) * (kT4Log2(l1) - 1) / 2 * 4096;
+}
+constexpr int kT4Size = 10 * 4096;
 
 // Launch; returns cudaErrorInvalidValue for L outside [4096, 65536].
 cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s);

@@ -27,15 +27,16 @@ inline void fill_twiddles(float2* tw) {
 }
 
 // Four-step twiddles of the spectrum-apply kernel (layout in fused.cuh):
-// exp(+2 pi i m / L) with m = q n2 mod L, in double, rounded once.
+// exp(+2 pi i m / L) with m = 2^b n2 mod L, in double, rounded once.
 inline void fill_four_step(float2* t4) {
   const double pi = 3.14159265358979323846;
   for (int l1 = 2; l1 <= 16; l1 *= 2) {
     const long long L = 4096LL * l1;
-    for (int q = 0; q < l1; ++q)
+    for (int b = 0; b < kT4Log2(l1); ++b)
       for (int n2 = 0; n2 < 4096; ++n2) {
-        const double a = 2.0 * pi * (double)(((long long)q * n2) % L) / (double)L;
-        t4[kT4Offset(l1) + q * 4096 + n2] = make_float2((float)std::cos(a), (float)std::sin(a));
+        const long long q = 1LL << b;
+        const double a = 2.0 * pi * (double)((q * n2) % L) / (double)L;
+        t4[kT4Offset(l1) + b * 4096 + n2] = make_float2((float)std::cos(a), (float)std::sin(a));
       }
   }
 }
