@@ -642,6 +642,13 @@ def run_plain(args) -> None:
                 pe.append((a, b))
         torch.cuda.synchronize()
         direct = [a.elapsed_time(b) for a, b in pe]
+        dcg.dc_profile_enable(ctx, True)
+        for _ in range(200):
+            dcg.doppler_resample(ctx, xd, yd, cfg.fs, cfg.fc, cfg.v_r, mode=mode)
+            dcg.iono_correct(ctx, yd, od, cfg.fs, cfg.fc, cfg.tec)
+        torch.cuda.synchronize()
+        kern = {k: 1e3 * vv[2] / vv[0] for k, vv in dcg.dc_profile_read(ctx).items()}
+        dcg.dc_profile_enable(ctx, False)
         t0 = time.perf_counter()
         reps = 0
         while True:
@@ -655,6 +662,7 @@ def run_plain(args) -> None:
             "device_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
             "host_ms": {"p50": float(np.percentile(host_ms, 50)), "p99": float(np.percentile(host_ms, 99))},
             "graph_launches_per_pulse": launches, "replays": R,
+            "kernel_us": {k: round(vv, 2) for k, vv in kern.items()},
             "plain_path": {"what": "doppler_resample + iono_correct calls, device time",
                            "p50_ms": float(np.percentile(direct, 50)),
                            "p99_ms": float(np.percentile(direct, 99)),

@@ -99,16 +99,12 @@ template <int CL> DC_DEV void cluster_sync() {
   if constexpr (CL > 1) cg::this_cluster().sync();
   else __syncthreads();
 }
-// Split cluster barrier: arrive (release: our reads of peers' shared memory
-// are done) as soon as the last remote values are consumed, wait (acquire)
-// only before exiting, so a CTA's shared memory outlives its peers' reads.
-template <int CL> DC_DEV void cluster_arrive() {
-  if constexpr (CL > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
+// Split cluster barrier: arrive early (relaxed: it only publishes mbarrier
+// initialisation, ordered by fence.mbarrier_init), wait (acquire) just
+// before the first remote access.
 template <int CL> DC_DEV void cluster_wait() {
   if constexpr (CL > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-
 template <int CL> DC_DEV void cluster_arrive_relaxed() {
   if constexpr (CL > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
@@ -131,8 +127,13 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
   constexpr int CL = L1 / ROWS;              // CTAs per cluster (per transform)
   constexpr int NT = ROWS * kRowThreads;
   constexpr int COLS = kRowN / CL;           // columns per CTA in the column passes
+  constexpr int PER = COLS / kRowThreads;    // columns per thread
   constexpr int LOG2L = 12 + LOG2L1;
-  extern __shared__ __align__(128) float2 sm[];   // [ROWS][2][kRowPitch]: per row, buffers A and B
+  // [ROWS][2][kRowPitch]: per row, buffers A and B; FULL with L1 > 1 adds
+  // [L1][COLS] for the inverse rows received from the cluster
+  extern __shared__ __align__(128) float2 sm[];
+  static_assert(ROWS == 1, "one row per CTA");
+  __shared__ __align__(8) unsigned long long bar_r;
 
   const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int item = blockIdx.x / CL;
@@ -152,6 +153,12 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
       v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
     }
   } else {
+    if constexpr (OP == FUSED_FULL) {
+      if (t == 0) {                            // published by the cluster barrier below
+        mbar_init(&bar_r, 1);
+        mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
+      }
+    }
     // forward columns (length L1) of this CTA's column range, times
     // W_L^(n2 k1), scattered to the rows' owners
     for (int c = t; c < COLS; c += NT) {
@@ -194,8 +201,7 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
   }
   // B was last read before the forward's second barrier; A (read by the
   // forward's stage 3) is next written after the inverse's first barrier.
-  row4096<+1>(v, bufB, bufA, j, a.tw);         // result exchanged last through A
-  float2* out_buf = bufB;                      // free: last read before a barrier
+  row4096<+1>(v, bufB, bufA, j, a.tw);
 
   // ------------------------------------------------------------ output side
   if constexpr (LOG2L1 == 0) {
@@ -206,36 +212,38 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
     }
     return;
   } else {
-    // four-step twiddle W_L^(-n2 k1), n2 = j + 256 r:
-    //   = W_L^(-j k1) * W_(16 L1)^(-r k1)   (second factor uniform in the CTA)
-    if (k1) {
-      const float2 a_j = tw_big<+1>(a.tw, (uint32_t)(j * k1), LOG2L);
+    // inverse row outputs X[n2 = j + 256 r] go to the owner of column n2
+    // (asynchronous remote stores counted on its receive barrier); the
+    // owner applies W_L^(-n2 q) and runs its inverse columns
+    float2* R = sm + 2 * kRowPitch;
+    const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
+    const uint32_t b_loc = smem_addr(&bar_r);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        // W_(16 L1)^(-r k1) = W4096^(-(r k1 mod 16 L1) * 256 / L1)
-        const int e = ((r * k1) & (16 * L1 - 1)) * (256 / L1);
-        v[r] = cmul(v[r], cmul(a_j, tw_m<+1>(a.tw, e)));
-      }
+    for (int r = 0; r < 16; ++r) {
+      const int owner = r / PER;
+      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));
+      st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
     }
+    const float2* T = a.t4 + kT4Offset(L1);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) out_buf[pad16(j + 256 * r)] = v[r];
-    cluster_sync<CL>();
-    const int out_off = kRowPitch;             // buffer B of each row
-    for (int c = t; c < COLS; c += NT) {
+    for (int p = 0; p < PER; ++p) {
+      const int c = j + 256 * p;
       const int n2 = rank * COLS + c;
+      float2 w[4];
+#pragma unroll
+      for (int b = 0; b < LOG2L1; ++b) w[b] = __ldg(T + b * kRowN + n2);   // W_L^(-2^b n2)
+      if (p == 0) mbar_wait_cluster_bounded(&bar_r, 0, a.err);
       float2 col[L1];
 #pragma unroll
-      for (int q = 0; q < L1; ++q)
-        col[q] = row_of<CL>(sm, q / ROWS)[(2 * (q % ROWS)) * kRowPitch + out_off + pad16(n2)];
+      for (int q = 0; q < L1; ++q) col[q] = R[q * COLS + c];
+      apply_powers<L1>(col, w);
       dft<L1, +1>(col);
-      if (c + NT >= COLS) cluster_arrive<CL>();  // same iteration for every thread
 #pragma unroll
       for (int n1 = 0; n1 < L1; ++n1) {
         const int n = n2 + kRowN * n1;
         if (n < I.n_out) __stcs(I.dst + n, col[n1]);
       }
     }
-    cluster_wait<CL>();                        // peers may still read our rows
   }
 }
 
@@ -246,7 +254,8 @@ cudaError_t launch_one(const FusedArgs& a, cudaStream_t s) {
   constexpr int ROWS = L1 >= kRowsPerCta ? kRowsPerCta : 1;
   constexpr int CL = L1 / ROWS;
   constexpr int NT = ROWS * kRowThreads;
-  const size_t smem = sizeof(float2) * ROWS * 2 * kRowPitch;
+  const size_t smem =
+      sizeof(float2) * (ROWS * 2 * kRowPitch + (OP == FUSED_FULL && L1 > 1 ? kRowN : 0));
   auto k = fused_kernel<LOG2L1, OP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
