@@ -49,15 +49,19 @@ DC_DEV df df_mul_f(df a, float k) {
   df p = two_prod(a.hi, k);
   return two_sum(p.hi, fmaf(a.lo, k, p.lo));
 }
-// a / b, both double-float
+// a / b, both double-float.  One reciprocal of b.hi serves both quotient
+// steps: q1 = a.hi / b.hi to a couple of ulps, the remainder
+// a - q1 b is formed exactly (two_prod, Sterbenz), and its quotient q2 only
+// needs float accuracy relative to itself (|q2| ~ 2^-23 |q1|).
 DC_DEV df df_div(df a, df b) {
-  float q1 = __fdiv_rn(a.hi, b.hi);
+  const float rb = __frcp_rn(b.hi);
+  const float q1 = __fmul_rn(a.hi, rb);
   df p = two_prod(q1, b.hi);
-  float r = __fsub_rn(a.hi, p.hi);          // exact: q1*b.hi is within an ulp of a.hi
+  float r = __fsub_rn(a.hi, p.hi);          // exact: q1*b.hi is within a few ulps of a.hi
   r = __fsub_rn(r, p.lo);
   r = __fadd_rn(r, a.lo);
   r = fmaf(-q1, b.lo, r);
-  float q2 = __fdiv_rn(r, b.hi);
+  const float q2 = __fmul_rn(r, rb);
   return two_sum(q1, q2);
 }
 
