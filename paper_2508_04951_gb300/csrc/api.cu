@@ -310,14 +310,17 @@ dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, 
   dc_status st = upload(c, wp, item_at, s, &dwp);
   if (st) return st;
   size_t at = item_at + ((wp.size() * sizeof(float) + 255) & ~(size_t)255);
-  // Split into the tiled launch (32 taps, |delta| <= 0.01) and the direct one.
-  std::vector<RsItem> tiled, direct;
+  // Split into the tiled launches (32 taps, |delta| <= 0.01; 8 outputs per
+  // lane while the quadratic weights hold over 256 outputs, else 4) and the
+  // direct one.
+  std::vector<RsItem> tiled8, tiled4, direct;
   for (auto& it : items) {
-    const double dl = (double)it.dl_hi + (double)it.dl_lo;
-    (o.taps == 32 && std::fabs(dl) <= kRsTiledMaxDelta ? tiled : direct).push_back(it);
+    const double dl = std::fabs((double)it.dl_hi + (double)it.dl_lo);
+    if (o.taps != 32 || dl > kRsTiledMaxDelta) direct.push_back(it);
+    else (resample_q(dl) == 8 ? tiled8 : tiled4).push_back(it);
   }
-  for (int pass = 0; pass < 2; ++pass) {
-    auto& v = pass == 0 ? tiled : direct;
+  for (int pass = 0; pass < 3; ++pass) {
+    auto& v = pass == 0 ? tiled8 : pass == 1 ? tiled4 : direct;
     if (v.empty()) continue;
     int tiles = 0;
     for (auto& it : v) {
@@ -336,8 +339,9 @@ dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, 
     a.err = c->err;
     long long outs = 0;
     for (auto& it : v) outs += it.n_out;
-    Phase ph(c, pass == 0 ? PH_RS_TILED : PH_RS_DIRECT, s, outs);
-    cudaError_t e = pass == 0 ? launch_resample_tiled32(a, s) : launch_resample_direct(a, s);
+    Phase ph(c, pass < 2 ? PH_RS_TILED : PH_RS_DIRECT, s, outs);
+    cudaError_t e = pass < 2 ? launch_resample_tiled32(a, pass == 0 ? 8 : 4, s)
+                             : launch_resample_direct(a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "resample launch");
   }
   return DC_OK;

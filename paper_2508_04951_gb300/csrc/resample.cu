@@ -107,50 +107,71 @@ __global__ void __launch_bounds__(kRsThreads) resample_direct_kernel(RsArgs a) {
 
 // ------------------------------------------------------------- tiled
 DC_DEV uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-DC_DEV int wpad(int i) { return i + (i >> 2); }   // 4 consecutive outputs per lane
 
-constexpr int kRsQ = 4;                  // consecutive outputs per lane
-constexpr int kRsW = 32 * kRsQ;          // outputs per warp tile
+// Q consecutive outputs per lane (4 or 8): a warp tile is 32 Q outputs and
+// kRsTile / Q threads cover the 1024-output CTA tile.
 constexpr int kWaitLimit = 1 << 22;      // bounded mbarrier polls
 // Largest move of e across a warp tile for the quadratic weights: the
 // interpolation error is about 0.064 |h'''| (span/2)^3 <= 2e-7 per weight.
-constexpr float kQuadSpan = 0.015f;
+constexpr float kQuadSpan = kRsQuadSpan;
 
-// Inner product loop of one lane over all taps: outputs ow + 4 lane + q,
-// inputs at padded window positions P0 + m + ((R0 + m) >> 2) -- R0, the
-// warp-uniform alignment of the window start, is a template parameter, so
-// every load has a constant offset.
-template <int TAPS, int R0>
+// Bank-spread window layout: element i at i + i / Q, so that lane l's
+// first tap input (Q l + const) lands on bank pair (Q + 1) l + const.
+template <int LQ> DC_DEV int wpad(int i) { return i + (i >> LQ); }
+
+// Inner product loop of one lane over all taps: outputs ow + Q lane + q,
+// inputs at padded window positions P0 + m + ((R0 + m) >> log2 Q) -- R0,
+// the warp-uniform alignment of the window start, is a template parameter,
+// so every load has a constant offset.  The Q inputs of a tap slide by one
+// per tap, so each tap loads one new input and one weight triple.
+template <int TAPS, int LQ, int R0>
 DC_DEV void tap_loop(const float2* __restrict__ w0, const float4* __restrict__ wts,
-                     const float (&sq)[kRsQ], float2 (&acc)[kRsQ]) {
-  float2 xw[kRsQ];
+                     const float (&sq)[1 << LQ], float2 (&acc)[1 << LQ]) {
+  constexpr int Q = 1 << LQ;
+  float2 xw[Q];
 #pragma unroll
-  for (int q = 0; q < kRsQ; ++q) xw[q] = w0[q + ((R0 + q) >> 2)];
+  for (int q = 0; q < Q; ++q) xw[q] = w0[q + ((R0 + q) >> LQ)];
 #pragma unroll
   for (int t = 0; t < TAPS; ++t) {
     const float4 w = wts[t];
 #pragma unroll
-    for (int q = 0; q < kRsQ; ++q) {
+    for (int q = 0; q < Q; ++q) {
       const float h = fmaf(fmaf(w.z, sq[q], w.y), sq[q], w.x);
       acc[q].x = fmaf(xw[q].x, h, acc[q].x);
       acc[q].y = fmaf(xw[q].y, h, acc[q].y);
     }
 #pragma unroll
-    for (int q = 0; q + 1 < kRsQ; ++q) xw[q] = xw[q + 1];
+    for (int q = 0; q + 1 < Q; ++q) xw[q] = xw[q + 1];
     if (t + 1 < TAPS) {
-      const int m = kRsQ + t;
-      xw[kRsQ - 1] = w0[m + ((R0 + m) >> 2)];
+      const int m = Q + t;
+      xw[Q - 1] = w0[m + ((R0 + m) >> LQ)];
     }
   }
 }
 
-template <int HALF>
-__global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
+// tap_loop with the window alignment r = B mod Q as a template argument.
+template <int TAPS, int LQ, int R0 = 0>
+DC_DEV void tap_loop_r(int r, const float2* __restrict__ w0, const float4* __restrict__ wts,
+                       const float (&sq)[1 << LQ], float2 (&acc)[1 << LQ]) {
+  if constexpr (R0 + 1 < (1 << LQ)) {
+    if (r != R0) {
+      tap_loop_r<TAPS, LQ, R0 + 1>(r, w0, wts, sq, acc);
+      return;
+    }
+  }
+  tap_loop<TAPS, LQ, R0>(w0, wts, sq, acc);
+}
+
+template <int HALF, int LQ>
+__global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a) {
+  constexpr int Q = 1 << LQ;
+  constexpr int NT = kRsTile / Q;          // threads
+  constexpr int W = 32 * Q;                // outputs per warp tile
   constexpr int TAPS = 2 * HALF;
-  constexpr int NW = kRsThreads / 32;
+  constexpr int NW = NT / 32;
   constexpr int WINMAX = kRsTile + 2 * HALF + 40;
   __shared__ __align__(16) float2 stage[WINMAX + 2];   // TMA window, later the output tile
-  __shared__ float2 win[WINMAX + WINMAX / 4 + 2];
+  __shared__ float2 win[WINMAX + WINMAX / Q + 2];
   __shared__ float4 wts[NW][TAPS];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ int s_item;
@@ -223,26 +244,26 @@ __global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
   }
   // Repack into the bank-spread layout; zero outside [0, N); ragged edges by
   // plain loads.
-  for (int idx = threadIdx.x; idx < wlen; idx += kRsThreads) {
+  for (int idx = threadIdx.x; idx < wlen; idx += NT) {
     const int gi = wlo + idx;
     float2 v = make_float2(0.f, 0.f);
     if (gi >= t0 && gi < t1) v = stage[idx + sh];
     else if (gi >= 0 && gi < I.n_in) v = __ldg(I.x + gi);
-    win[wpad(idx)] = v;
+    win[wpad<LQ>(idx)] = v;
   }
   __syncthreads();                           // window ready; stage is free again
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ow = o0 + warp * kRsW;
-  constexpr float H = 0.5f * (kRsW - 1);
+  const int ow = o0 + warp * W;
+  constexpr float H = 0.5f * (W - 1);
   int f0, f1, f2;
   float e0, e1, e2;
   rs_delay(I.dl_hi, I.dl_lo, (float)ow, f0, e0);
   rs_delay(I.dl_hi, I.dl_lo, (float)ow + H, f1, e1);
-  rs_delay(I.dl_hi, I.dl_lo, (float)(ow + kRsW - 1), f2, e2);
-  float2 acc[kRsQ];
+  rs_delay(I.dl_hi, I.dl_lo, (float)(ow + W - 1), f2, e2);
+  float2 acc[Q];
 #pragma unroll
-  for (int q = 0; q < kRsQ; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < Q; ++q) acc[q] = make_float2(0.f, 0.f);
 
   if (ow < I.n_out) {
     if (f0 == f2 && f0 == f1 && fabsf(e2 - e0) <= kQuadSpan) {
@@ -258,37 +279,32 @@ __global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
         wts[warp][t] = make_float4(hB, q1, q2, 0.f);
       }
       __syncwarp();
-      // Window index of output ow + 4 lane + q at tap t is B + 4 lane + m,
-      // m = q + t; with B = 4 b + r (r = B & 3, uniform in the warp) its
-      // padded position is 5 lane + B + b + m + ((r + m) >> 2).
+      // Window index of output ow + Q lane + q at tap t is B + Q lane + m,
+      // m = q + t; with B = Q b + r (r = B mod Q, uniform in the warp) its
+      // padded position is (Q + 1) lane + B + b + m + ((r + m) >> log2 Q).
       const int B = ow + f0 - HALF + 1 - wlo;
-      const int P0 = 5 * lane + B + (B >> 2);
-      float sq[kRsQ];
+      const int P0 = (Q + 1) * lane + B + (B >> LQ);
+      float sq[Q];
 #pragma unroll
-      for (int q = 0; q < kRsQ; ++q) sq[q] = (float)(lane * kRsQ + q) - H;
-      switch (B & 3) {
-        case 0: tap_loop<TAPS, 0>(win + P0, wts[warp], sq, acc); break;
-        case 1: tap_loop<TAPS, 1>(win + P0, wts[warp], sq, acc); break;
-        case 2: tap_loop<TAPS, 2>(win + P0, wts[warp], sq, acc); break;
-        default: tap_loop<TAPS, 3>(win + P0, wts[warp], sq, acc); break;
-      }
+      for (int q = 0; q < Q; ++q) sq[q] = (float)(lane * Q + q) - H;
+      tap_loop_r<TAPS, LQ>(B & (Q - 1), win + P0, wts[warp], sq, acc);
     } else {
       // floor(delta n) steps inside this warp tile, or e moves too far:
       // exact weights per output.
 #pragma unroll
-      for (int q = 0; q < kRsQ; ++q) {
-        const int i = ow + lane * kRsQ + q;
+      for (int q = 0; q < Q; ++q) {
+        const int i = ow + lane * Q + q;
         int fl;
         float e;
         rs_delay(I.dl_hi, I.dl_lo, (float)i, fl, e);
         const int m = i + fl - wlo;
         if (e == 0.f) {
-          acc[q] = win[wpad(m)];
+          acc[q] = win[wpad<LQ>(m)];
         } else {
           const float s_e = sinpif(e) * kInvPi;
           for (int k = -HALF + 1; k <= HALF; ++k) {
             const float h = tap_weight(a, e, s_e, k);
-            const float2 v = win[wpad(m + k)];
+            const float2 v = win[wpad<LQ>(m + k)];
             acc[q].x = fmaf(v.x, h, acc[q].x);
             acc[q].y = fmaf(v.y, h, acc[q].y);
           }
@@ -297,25 +313,28 @@ __global__ void __launch_bounds__(kRsThreads) resample_tiled_kernel(RsArgs a) {
     }
   }
   // Output tile through shared memory, then 16-byte coalesced stores.
-  float4* st4 = reinterpret_cast<float4*>(stage) + warp * (kRsW / 2) + lane * 2;
-  st4[0] = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
-  st4[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
+  float4* st4 = reinterpret_cast<float4*>(stage) + warp * (W / 2) + lane * (Q / 2);
+#pragma unroll
+  for (int q = 0; q < Q / 2; ++q)
+    st4[q] = make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
   __syncthreads();
   const int n_here = min(kRsTile, I.n_out - o0);
   float2* y = I.y + o0;
   if ((reinterpret_cast<uintptr_t>(y) & 15) == 0) {
     const float4* s4 = reinterpret_cast<const float4*>(stage);
-    for (int p = threadIdx.x; 2 * p + 1 < n_here; p += kRsThreads)
+    for (int p = threadIdx.x; 2 * p + 1 < n_here; p += NT)
       __stcs(reinterpret_cast<float4*>(y) + p, s4[p]);
     if ((n_here & 1) && threadIdx.x == 0) y[n_here - 1] = stage[n_here - 1];
   } else {
-    for (int p = threadIdx.x; p < n_here; p += kRsThreads) y[p] = stage[p];
+    for (int p = threadIdx.x; p < n_here; p += NT) y[p] = stage[p];
   }
 }
 
-cudaError_t launch_resample_tiled32(const RsArgs& a, cudaStream_t s) {
+cudaError_t launch_resample_tiled32(const RsArgs& a, int q, cudaStream_t s) {
   if (a.n_tiles <= 0) return cudaSuccess;
-  resample_tiled_kernel<16><<<a.n_tiles, kRsThreads, 0, s>>>(a);
+  if (q == 8) resample_tiled_kernel<16, 3><<<a.n_tiles, kRsTile / 8, 0, s>>>(a);
+  else if (q == 4) resample_tiled_kernel<16, 2><<<a.n_tiles, kRsTile / 4, 0, s>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -43,8 +43,14 @@ struct ExArgs {
 
 constexpr int kRsTile = 1024;     // outputs per CTA of the tiled kernel
 constexpr float kRsTiledMaxDelta = 0.01f;
+// The tiled kernel's warp tile is 32 q outputs (q = 8 or 4 per lane); its
+// per-tap quadratic weights need e to move at most kRsQuadSpan across it,
+// else the tile falls back to exact weights: q = 8 while
+// |delta| (256 - 1) <= kRsQuadSpan, q = 4 above.
+constexpr float kRsQuadSpan = 0.015f;
+inline int resample_q(double delta_abs) { return delta_abs * 255.0 <= 0.98 * kRsQuadSpan ? 8 : 4; }
 
-cudaError_t launch_resample_tiled32(const RsArgs& a, cudaStream_t s);
+cudaError_t launch_resample_tiled32(const RsArgs& a, int q, cudaStream_t s);
 cudaError_t launch_resample_direct(const RsArgs& a, cudaStream_t s);
 cudaError_t launch_exact_fp32(const ExArgs& a, int n_alpha, cudaStream_t s);
 

@@ -61,6 +61,7 @@ def noise(n, salt):
 @pytest.mark.parametrize("n,v,n_out", [
     (1, 7500.0, 1), (5, -8000.0, 9), (1000, 7500.0, 1000), (4096, -8000.0, 4096),
     (4097, 8000.0, 2500), (70001, 7500.0, 70001), (70001, -3e5, 70100),
+    (70001, 12000.0, 70001), (70001, -15000.0, 70001),   # 4 outputs per lane (|delta| ~ 1e-4)
     (5000, 1.4e6, 5000),              # delta ~ 0.0093: tiled kernel, many wrap tiles
     (5000, 3e6, 5000),                # delta ~ 0.02: direct kernel
     (3000, -2e7, 3300),               # alpha ~ 0.875
