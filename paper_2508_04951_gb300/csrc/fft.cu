@@ -165,22 +165,26 @@ __global__ void __launch_bounds__(kThreads) row_kernel(RowArgs a) {
 }
 
 // ------------------------------------------------------------ column pass
-// 16 columns per CTA, element p of column c at sm[p*16 + c]; consecutive
-// threads take consecutive columns, so global rows of 16 complex (128 B) are
-// read and written whole.
+// C = 4096 / M columns per CTA (32 KiB of shared memory for every M, and
+// 256 butterflies per radix-16 stage), element p of column c at sm[p*C + c];
+// consecutive threads take consecutive columns, so global rows of C complex
+// are read and written whole.
+template <int M> __host__ __device__ constexpr int col_width() { return 4096 / M; }
+
 template <int M, int R, int NS, int DIR>
 DC_DEV void col_stage(float2* sm, const float2* __restrict__ tw) {
+  constexpr int C = col_width<M>();
   constexpr int NB = M / R;
-  constexpr int TOTAL = NB * 16;
+  constexpr int TOTAL = NB * C;
   constexpr int PER = (TOTAL + kThreads - 1) / kThreads;
   float2 v[PER][R];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int b = threadIdx.x + kThreads * q;
     if (TOTAL % kThreads == 0 || b < TOTAL) {
-      const int c = b & 15, j = b >> 4;
+      const int c = b % C, j = b / C;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = sm[(j + r * NB) * 16 + c];
+      for (int r = 0; r < R; ++r) v[q][r] = sm[(j + r * NB) * C + c];
       if constexpr (NS > 1) {
         const int k = j % NS;
 #pragma unroll
@@ -195,11 +199,11 @@ DC_DEV void col_stage(float2* sm, const float2* __restrict__ tw) {
   for (int q = 0; q < PER; ++q) {
     const int b = threadIdx.x + kThreads * q;
     if (TOTAL % kThreads == 0 || b < TOTAL) {
-      const int c = b & 15, j = b >> 4;
+      const int c = b % C, j = b / C;
       const int k = j % NS;
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[(base + r * NS) * 16 + c] = v[q][r];
+      for (int r = 0; r < R; ++r) sm[(base + r * NS) * C + c] = v[q][r];
     }
   }
   __syncthreads();
@@ -216,39 +220,55 @@ DC_DEV void col_fft(float2* sm, const float2* __restrict__ tw) {
 // Column pass for M = L1 in [32, 256] (shared memory).
 template <int M, int OP>
 __global__ void __launch_bounds__(kThreads) col_kernel_smem(ColArgs a) {
-  __shared__ float2 sm[M * 16];
+  constexpr int C = col_width<M>();
+  __shared__ float2 sm[M * C];
   const int L2 = 1 << (a.log2L - a.log2L1);
-  const int cta_per_item = L2 >> 4;
+  const int cta_per_item = L2 / C;
   const int it = blockIdx.x / cta_per_item;
-  const int col0 = (blockIdx.x % cta_per_item) * 16;
+  const int col0 = (blockIdx.x % cta_per_item) * C;
   const FftItem& I = a.items[it];
   const float invL = 1.0f / (float)(1 << a.log2L);
 
-  for (int idx = threadIdx.x; idx < M * 16; idx += kThreads) {
-    const int c = idx & 15, p = idx >> 4;
-    const int n2 = col0 + c;
-    float2 v = make_float2(0.f, 0.f);
+  // all of a thread's loads first (the global source may not be proven
+  // apart from shared memory, which would serialise load/store pairs)
+  constexpr int PER = M * C / kThreads;
+  const int c = threadIdx.x % C, p0 = threadIdx.x / C;
+  constexpr int PSTEP = kThreads / C;
+  const int n2 = col0 + c;
+  float2 v[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int p = p0 + PSTEP * q;
     if (OP == COL_F1) {
       const int n = n2 + L2 * p;
-      if (n < I.n_valid) v = I.src[n];
+      v[q] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
     } else {
-      v = I.src[(size_t)p * L2 + n2];
+      v[q] = __ldg(I.src + (size_t)p * L2 + n2);
     }
-    sm[p * 16 + c] = v;
   }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) sm[(p0 + PSTEP * q) * C + c] = v[q];
   __syncthreads();
   col_fft<M, OP == COL_F1 ? -1 : +1>(sm, a.tw);
-  for (int idx = threadIdx.x; idx < M * 16; idx += kThreads) {
-    const int c = idx & 15, p = idx >> 4;
-    const int n2 = col0 + c;
-    float2 v = sm[p * 16 + c];
-    if (OP == COL_F1) {
-      // twiddle W_L^(n2 k1), k1 = p
-      v = cmul(v, tw_big<-1>(a.tw, (uint32_t)(n2 * p) & ((1u << a.log2L) - 1), a.log2L));
-      I.dst[(size_t)p * L2 + n2] = v;
-    } else {
-      const int n = n2 + L2 * p;
-      if (n < I.n_out) __stcs(I.dst + n, cscale(v, invL));
+#pragma unroll
+  for (int q = 0; q < PER; ++q) v[q] = sm[(p0 + PSTEP * q) * C + c];
+  if (OP == COL_F1) {
+    // twiddle W_L^(n2 k1), k1 = p0 + PSTEP q: W_L^(n2 p0) times the q-th
+    // power of W_L^(n2 PSTEP) (powers from the table values for 1, 2, 4, 8)
+    static_assert(PER == 16, "16 rows per thread");
+    const uint32_t mask = (1u << a.log2L) - 1;
+    float2 b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = tw_big<-1>(a.tw, (uint32_t)(n2 * (PSTEP << i)) & mask, a.log2L);
+    const float2 w0 = tw_big<-1>(a.tw, (uint32_t)(n2 * p0) & mask, a.log2L);
+    apply_powers<PER>(v, b);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) I.dst[(size_t)(p0 + PSTEP * q) * L2 + n2] = cmul(v[q], w0);
+  } else {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int n = n2 + L2 * (p0 + PSTEP * q);
+      if (n < I.n_out) __stcs(I.dst + n, cscale(v[q], invL));
     }
   }
 }
@@ -344,7 +364,7 @@ static cudaError_t launch_col_m(const ColArgs& a, cudaStream_t s) {
     const long long grid = (long long)a.n_items * (L2 / kThreads);
     col_kernel_reg<M, OP><<<(unsigned)grid, kThreads, 0, s>>>(a);
   } else {
-    const long long grid = (long long)a.n_items * (L2 / 16);
+    const long long grid = (long long)a.n_items * (L2 / col_width<M>());
     col_kernel_smem<M, OP><<<(unsigned)grid, kThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
