@@ -63,11 +63,20 @@ DC_DEV float tap_weight(const RsArgs& a, float e, float s_e, int k) {
   return sc * window_at(a.wpoly, k + a.half - 1, e);
 }
 
+// The item owning a tile: the last item with tile_begin <= tile (tile_begin
+// strictly increases).  One warp probes 32 evenly spaced items per round, so
+// the search takes ceil(log32 n_items) dependent loads instead of log2.
+// Every lane of the warp calls it and gets the answer.
 DC_DEV int find_item(const RsArgs& a, int tile) {
-  int lo = 0, hi = a.n_items - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.items[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = a.n_items;                  // items[lo].tile_begin <= tile < items[hi]
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) >> 5;
+    const int idx = lo + lane * step;
+    const bool ok = idx < hi && a.items[idx].tile_begin <= tile;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);   // lane 0 always set
+    lo += (31 - __clz((int)m)) * step;
+    hi = min(hi, lo + step);
   }
   return lo;
 }
@@ -76,7 +85,10 @@ DC_DEV int find_item(const RsArgs& a, int tile) {
 __global__ void __launch_bounds__(kRsThreads) resample_direct_kernel(RsArgs a) {
   __shared__ int s_item;
   const int tile = blockIdx.x;
-  if (threadIdx.x == 0) s_item = find_item(a, tile);
+  if (threadIdx.x < 32) {
+    const int it = find_item(a, tile);
+    if (threadIdx.x == 0) s_item = it;
+  }
   __syncthreads();
   const RsItem& I = a.items[s_item];
   const int o0 = (tile - I.tile_begin) * kRsTile;
@@ -177,7 +189,10 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   __shared__ int s_item;
 
   const int tile = blockIdx.x;
-  if (threadIdx.x == 0) s_item = find_item(a, tile);
+  if (threadIdx.x < 32) {
+    const int it = find_item(a, tile);
+    if (threadIdx.x == 0) s_item = it;
+  }
   __syncthreads();
   const RsItem& I = a.items[s_item];
   const int o0 = (tile - I.tile_begin) * kRsTile;
