@@ -10,12 +10,13 @@
 //    is the paper's Algorithm 1 shape and the library's general path.
 //  * tiled (|alpha - 1| <= 0.01, 32 taps): a CTA owns 1024 consecutive outputs;
 //    its input window is staged in shared memory by one TMA bulk copy; each
-//    warp owns 128 outputs; when e moves by at most 0.015 of a sample across
-//    them (|alpha - 1| <= 1.1e-4, i.e. |v_r| <= 17 km/s) each tap weight is
-//    the quadratic through its exact values at the warp tile's first, middle
-//    and last output (error <= 2e-7; 2e-8 at |v_r| <= 8 km/s).  Other warp
-//    tiles, and tiles where floor(delta n) steps, use exact per-output weights
-//    read against the same staged window.
+//    lane owns Q = 8 consecutive outputs (a warp 256) while e moves by at most
+//    0.015 of a sample across a warp tile (|alpha - 1| <= 5.8e-5, |v_r| <=
+//    8.7 km/s), else Q = 4 (|alpha - 1| <= 1.1e-4, |v_r| <= 17 km/s); each tap
+//    weight is then the quadratic through its exact values at the warp tile's
+//    first, middle and last output (error <= 2e-7).  Other warp tiles, and
+//    tiles where floor(delta n) steps, use exact per-output weights read
+//    against the same staged window.
 #include "resample.cuh"
 
 namespace dc {
@@ -132,17 +133,18 @@ constexpr float kQuadSpan = kRsQuadSpan;
 template <int LQ> DC_DEV int wpad(int i) { return i + (i >> LQ); }
 
 // Inner product loop of one lane over all taps: outputs ow + Q lane + q,
-// inputs at padded window positions P0 + m + ((R0 + m) >> log2 Q) -- R0,
-// the warp-uniform alignment of the window start, is a template parameter,
-// so every load has a constant offset.  The Q inputs of a tap slide by one
-// per tap, so each tap loads one new input and one weight triple.
-template <int TAPS, int LQ, int R0>
-DC_DEV void tap_loop(const float2* __restrict__ w0, const float4* __restrict__ wts,
+// inputs at padded window positions P0 + m + ((r + m) >> log2 Q), r the
+// warp-uniform alignment of the window start.  The Q inputs of a tap slide
+// by one per tap, so each tap loads one new input and one weight triple.
+// (r is a run-time value: one instance of this fully unrolled loop instead of
+// Q keeps the kernel's code within the instruction cache.)
+template <int TAPS, int LQ>
+DC_DEV void tap_loop(int r, const float2* __restrict__ w0, const float4* __restrict__ wts,
                      const float (&sq)[1 << LQ], float2 (&acc)[1 << LQ]) {
   constexpr int Q = 1 << LQ;
   float2 xw[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) xw[q] = w0[q + ((R0 + q) >> LQ)];
+  for (int q = 0; q < Q; ++q) xw[q] = w0[q + ((r + q) >> LQ)];
 #pragma unroll
   for (int t = 0; t < TAPS; ++t) {
     const float4 w = wts[t];
@@ -156,22 +158,9 @@ DC_DEV void tap_loop(const float2* __restrict__ w0, const float4* __restrict__ w
     for (int q = 0; q + 1 < Q; ++q) xw[q] = xw[q + 1];
     if (t + 1 < TAPS) {
       const int m = Q + t;
-      xw[Q - 1] = w0[m + ((R0 + m) >> LQ)];
+      xw[Q - 1] = w0[m + ((r + m) >> LQ)];
     }
   }
-}
-
-// tap_loop with the window alignment r = B mod Q as a template argument.
-template <int TAPS, int LQ, int R0 = 0>
-DC_DEV void tap_loop_r(int r, const float2* __restrict__ w0, const float4* __restrict__ wts,
-                       const float (&sq)[1 << LQ], float2 (&acc)[1 << LQ]) {
-  if constexpr (R0 + 1 < (1 << LQ)) {
-    if (r != R0) {
-      tap_loop_r<TAPS, LQ, R0 + 1>(r, w0, wts, sq, acc);
-      return;
-    }
-  }
-  tap_loop<TAPS, LQ, R0>(w0, wts, sq, acc);
 }
 
 template <int HALF, int LQ>
@@ -197,7 +186,7 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   const RsItem& I = a.items[s_item];
   const int o0 = (tile - I.tile_begin) * kRsTile;
 
-  // Input window of the CTA's 1024 outputs.
+  // Input window of the CTA's kRsTile outputs.
   int flA, flB;
   float eA, eB;
   rs_delay(I.dl_hi, I.dl_lo, (float)o0, flA, eA);
@@ -302,7 +291,7 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
       float sq[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) sq[q] = (float)(lane * Q + q) - H;
-      tap_loop_r<TAPS, LQ>(B & (Q - 1), win + P0, wts[warp], sq, acc);
+      tap_loop<TAPS, LQ>(B & (Q - 1), win + P0, wts[warp], sq, acc);
     } else {
       // floor(delta n) steps inside this warp tile, or e moves too far:
       // exact weights per output.

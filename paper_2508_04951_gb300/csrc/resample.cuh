@@ -15,7 +15,7 @@ struct RsItem {
   float2* y;           // output samples [n_out]
   int n_in, n_out;
   float dl_hi, dl_lo;  // delta = alpha - 1 as a double-float
-  int tile_begin;      // first 1024-output tile of this item in the launch
+  int tile_begin;      // first kRsTile-output tile of this item in the launch
 };
 
 struct RsArgs {
@@ -41,7 +41,7 @@ struct ExArgs {
   int n_in, n_out, n_pulses;
 };
 
-constexpr int kRsTile = 1024;     // outputs per CTA of the tiled kernel
+constexpr int kRsTile = 1024;     // outputs per CTA of the resampling kernels
 constexpr float kRsTiledMaxDelta = 0.01f;
 // The tiled kernel's warp tile is 32 q outputs (q = 8 or 4 per lane); its
 // per-tap quadratic weights need e to move at most kRsQuadSpan across it,
