@@ -149,6 +149,15 @@ PhaseParams phase_params(double fs, double fc, double tec_tecu, int log2L) {
   split(fs / (double)(1LL << log2L), p.d_hi, p.d_lo);
   p.log2L = log2L;
   p.enabled = tec_tecu != 0.0;
+  // Stepped phase runs (16 bins, s d = fs / 4096): the largest step over the
+  // band is |A| (fs / 4096) / f_min^2; 15 steps of relative error ~3.3e-7
+  // stay within 1e-7 rad while it is <= 0.02 rad.  RF sampling (a bin at
+  // f = 0) always evaluates every bin.
+  p.run = 1;
+  if (fc > 0.0) {
+    const double fmin = fc - 0.5 * fs;
+    if (fmin > 0.0 && std::fabs(A) * (fs / 4096.0) / (fmin * fmin) <= 0.02) p.run = 16;
+  }
   return p;
 }
 

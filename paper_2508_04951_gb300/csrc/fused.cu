@@ -191,16 +191,31 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
     for (int r = 0; r < 16; ++r) I.dst[(size_t)k1 * kRowN + j + 256 * r] = v[r];
     return;
   }
+  // phase of bin k = k1 + L1 k2: regroup through B (free: last read before
+  // the forward's second barrier) so each thread owns 16 consecutive k2
+  if (I.ph.enabled) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) bufB[pad16(j + 256 * r)] = v[r];
+    __syncthreads();
+    float2 u[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) u[i] = bufB[pad16(16 * j + i)];
+    iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bufB[pad16(16 * j + i)] = u[i];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = bufB[pad16(j + 256 * r)];
+    __syncthreads();                           // the inverse row writes B first
+  }
   {
     const float invL = 1.0f / (float)(1 << LOG2L);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const float2 w = I.ph.enabled ? iono_factor(I.ph, k1 + L1 * (j + 256 * r)) : make_float2(1.f, 0.f);
-      v[r] = cscale(cmul(v[r], w), invL);
-    }
+    for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
   }
-  // B was last read before the forward's second barrier; A (read by the
-  // forward's stage 3) is next written after the inverse's first barrier.
+  // B was last read before the forward's second barrier (or just above); A
+  // (read by the forward's stage 3) is next written after the inverse's
+  // first barrier.
   row4096<+1>(v, bufB, bufA, j, a.tw);
 
   // ------------------------------------------------------------ output side
@@ -421,8 +436,21 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_mid_kernel(RowArgs a) {
   for (int r = 0; r < 16; ++r) v[r] = src[j + 256 * r];
   row4096<-1>(v, bufA, bufB, j, a.tw);
   if (I.ph.enabled) {
+    // phase of bin k = k1 + L1 k2, each thread on 16 consecutive k2 (A is
+    // free: last read before the forward's second barrier)
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], iono_factor(I.ph, k1 + L1 * (j + 256 * r)));
+    for (int r = 0; r < 16; ++r) bufA[pad16(j + 256 * r)] = v[r];
+    __syncthreads();
+    float2 u[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) u[i] = bufA[pad16(16 * j + i)];
+    iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bufA[pad16(16 * j + i)] = u[i];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = bufA[pad16(j + 256 * r)];
+    __syncthreads();                           // the inverse row writes A first
   }
   row4096<+1>(v, bufA, bufB, j, a.tw);
   if (k1) {

@@ -102,6 +102,7 @@ extern "C" dc_status iono_correct_noalloc(const dc_c64* x, long long n, dc_c64* 
   split(fs / (double)(1LL << log2L), it.ph.d_hi, it.ph.d_lo);
   it.ph.log2L = log2L;
   it.ph.enabled = tec_tecu != 0.0;
+  it.ph.run = 1;                               // every bin evaluated in full
   it.n_valid = (int)n;
   it.n_out = (int)n;
 

@@ -163,6 +163,22 @@ def test_iono_correct_matches_oracle(dcg, ctx, n, tec):
     assert rel(host(yd), ref) <= TOL
 
 
+@pytest.mark.parametrize("n", [5000, 65536, 200000])
+@pytest.mark.parametrize("tec", [150.0, 230.0, 245.0])
+def test_iono_phase_accuracy(dcg, ctx, n, tec):
+    # The phase of 16 neighbouring bins may be stepped from the first one (the
+    # host allows it while the step bound keeps the error under 1e-7 rad: TEC
+    # 150 and 230 here at fc = 1 GHz, fs = 20 MHz; 245 is past the bound and
+    # evaluates every bin).  Held to 1e-6, ten times tighter than the path's
+    # tolerance, so a loss of phase accuracy shows.
+    x = noise(n, salt=n % 29)
+    xd, yd = to_dev(x), empty(n)
+    dcg.iono_correct(ctx, xd, yd, 20e6, 1e9, tec)
+    dcg.dc_check(ctx)
+    ref = oracle.iono_correct(x.astype(np.complex128), 20e6, 1e9, tec)
+    assert rel(host(yd), ref) <= 1e-6
+
+
 def test_iono_zero_tec_and_in_place(dcg, ctx):
     x = noise(30000, salt=5)
     xd = to_dev(x)
