@@ -133,18 +133,17 @@ constexpr float kQuadSpan = kRsQuadSpan;
 template <int LQ> DC_DEV int wpad(int i) { return i + (i >> LQ); }
 
 // Inner product loop of one lane over all taps: outputs ow + Q lane + q,
-// inputs at padded window positions P0 + m + ((r + m) >> log2 Q), r the
-// warp-uniform alignment of the window start.  The Q inputs of a tap slide
-// by one per tap, so each tap loads one new input and one weight triple.
-// (r is a run-time value: one instance of this fully unrolled loop instead of
-// Q keeps the kernel's code within the instruction cache.)
+// inputs at padded slice positions m + (m >> log2 Q) from the lane's base
+// (the slice starts at the warp tile's first input, so every offset is a
+// compile-time constant).  The Q inputs of a tap slide by one per tap, so
+// each tap loads one new input and one weight triple.
 template <int TAPS, int LQ>
-DC_DEV void tap_loop(int r, const float2* __restrict__ w0, const float4* __restrict__ wts,
+DC_DEV void tap_loop(const float2* __restrict__ w0, const float4* __restrict__ wts,
                      const float (&sq)[1 << LQ], float2 (&acc)[1 << LQ]) {
   constexpr int Q = 1 << LQ;
   float2 xw[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) xw[q] = w0[q + ((r + q) >> LQ)];
+  for (int q = 0; q < Q; ++q) xw[q] = w0[q + (q >> LQ)];
 #pragma unroll
   for (int t = 0; t < TAPS; ++t) {
     const float4 w = wts[t];
@@ -158,7 +157,7 @@ DC_DEV void tap_loop(int r, const float2* __restrict__ w0, const float4* __restr
     for (int q = 0; q + 1 < Q; ++q) xw[q] = xw[q + 1];
     if (t + 1 < TAPS) {
       const int m = Q + t;
-      xw[Q - 1] = w0[m + ((r + m) >> LQ)];
+      xw[Q - 1] = w0[m + (m >> LQ)];
     }
   }
 }
@@ -171,8 +170,11 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   constexpr int TAPS = 2 * HALF;
   constexpr int NW = NT / 32;
   constexpr int WINMAX = kRsTile + 2 * HALF + 40;
-  __shared__ __align__(16) float2 stage[WINMAX + 2];   // TMA window, later the output tile
-  __shared__ float2 win[WINMAX + WINMAX / Q + 2];
+  constexpr int WWIN = W + TAPS + 3;                   // a warp's slice (|f2 - f0| <= 4)
+  constexpr int WSTRIDE = ((WWIN + (WWIN >> LQ) + 1) | 1) + 1;   // even: 16-byte aligned slices
+  static_assert(WSTRIDE >= W, "a slice stages the warp's outputs");
+  __shared__ __align__(16) float2 stage[WINMAX + 2];   // the CTA's window, by TMA
+  __shared__ __align__(16) float2 win[NW * WSTRIDE];
   __shared__ float4 wts[NW][TAPS];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ int s_item;
@@ -246,91 +248,106 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
       return;
     }
   }
-  // Repack into the bank-spread layout; zero outside [0, N); ragged edges by
-  // plain loads.
-  for (int idx = threadIdx.x; idx < wlen; idx += NT) {
-    const int gi = wlo + idx;
-    float2 v = make_float2(0.f, 0.f);
-    if (gi >= t0 && gi < t1) v = stage[idx + sh];
-    else if (gi >= 0 && gi < I.n_in) v = __ldg(I.x + gi);
-    win[wpad<LQ>(idx)] = v;
-  }
-  __syncthreads();                           // window ready; stage is free again
-
+  // Each warp repacks its own slice of the window -- global positions
+  // G .. G + WWIN - 1, G = ow + min(f0, f2) - HALF + 1 -- into a private,
+  // bank-spread region, so tap offsets are compile-time constants and no CTA
+  // barrier follows; the region then stages the warp's outputs.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ow = o0 + warp * W;
+  if (ow >= I.n_out) return;                   // warp-uniform: nothing to write
   constexpr float H = 0.5f * (W - 1);
   int f0, f1, f2;
   float e0, e1, e2;
   rs_delay(I.dl_hi, I.dl_lo, (float)ow, f0, e0);
   rs_delay(I.dl_hi, I.dl_lo, (float)ow + H, f1, e1);
   rs_delay(I.dl_hi, I.dl_lo, (float)(ow + W - 1), f2, e2);
+  if (abs(f2 - f0) > 4) {                      // |delta| too large for the slice
+    if (lane == 0) atomicExch(a.err, 2);
+    return;
+  }
+  const int fmin = min(f0, f2);
+  const int G = ow + fmin - HALF + 1;
+  float2* ww = win + warp * WSTRIDE;
+  for (int i = lane; i < WWIN; i += 32) {
+    const int gi = G + i;
+    float2 v = make_float2(0.f, 0.f);
+    if (gi >= t0 && gi < t1) v = stage[gi - wlo + sh];
+    else if (gi >= 0 && gi < I.n_in) v = __ldg(I.x + gi);
+    ww[wpad<LQ>(i)] = v;
+  }
+  __syncwarp();
+
   float2 acc[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) acc[q] = make_float2(0.f, 0.f);
-
-  if (ow < I.n_out) {
-    if (f0 == f2 && f0 == f1 && fabsf(e2 - e0) <= kQuadSpan) {
-      // Quadratic weights per tap through the three nodes s = -H, 0, +H.
-      const float s0 = sinpif(e0) * kInvPi, s1 = sinpif(e1) * kInvPi, s2 = sinpif(e2) * kInvPi;
-      for (int t = lane; t < TAPS; t += 32) {
-        const int k = t - HALF + 1;
-        const float hA = tap_weight(a, e0, s0, k);
-        const float hB = tap_weight(a, e1, s1, k);
-        const float hC = tap_weight(a, e2, s2, k);
-        const float q1 = (hC - hA) * (0.5f / H);
-        const float q2 = (hC - 2.f * hB + hA) * (0.5f / (H * H));
-        wts[warp][t] = make_float4(hB, q1, q2, 0.f);
-      }
-      __syncwarp();
-      // Window index of output ow + Q lane + q at tap t is B + Q lane + m,
-      // m = q + t; with B = Q b + r (r = B mod Q, uniform in the warp) its
-      // padded position is (Q + 1) lane + B + b + m + ((r + m) >> log2 Q).
-      const int B = ow + f0 - HALF + 1 - wlo;
-      const int P0 = (Q + 1) * lane + B + (B >> LQ);
-      float sq[Q];
+  if (f0 == f2 && f0 == f1 && fabsf(e2 - e0) <= kQuadSpan) {
+    // Quadratic weights per tap through the three nodes s = -H, 0, +H.
+    const float s0 = sinpif(e0) * kInvPi, s1 = sinpif(e1) * kInvPi, s2 = sinpif(e2) * kInvPi;
+    for (int t = lane; t < TAPS; t += 32) {
+      const int k = t - HALF + 1;
+      const float hA = tap_weight(a, e0, s0, k);
+      const float hB = tap_weight(a, e1, s1, k);
+      const float hC = tap_weight(a, e2, s2, k);
+      const float q1 = (hC - hA) * (0.5f / H);
+      const float q2 = (hC - 2.f * hB + hA) * (0.5f / (H * H));
+      wts[warp][t] = make_float4(hB, q1, q2, 0.f);
+    }
+    __syncwarp();
+    // Output ow + Q lane + q at tap t reads slice position Q lane + q + t,
+    // padded (Q + 1) lane + m + (m >> log2 Q) with m = q + t.
+    float sq[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) sq[q] = (float)(lane * Q + q) - H;
-      tap_loop<TAPS, LQ>(B & (Q - 1), win + P0, wts[warp], sq, acc);
-    } else {
-      // floor(delta n) steps inside this warp tile, or e moves too far:
-      // exact weights per output.
+    for (int q = 0; q < Q; ++q) sq[q] = (float)(lane * Q + q) - H;
+    tap_loop<TAPS, LQ>(ww + (Q + 1) * lane, wts[warp], sq, acc);
+  } else {
+    // floor(delta n) steps inside this warp tile, or e moves too far:
+    // exact weights per output.
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int i = ow + lane * Q + q;
-        int fl;
-        float e;
-        rs_delay(I.dl_hi, I.dl_lo, (float)i, fl, e);
-        const int m = i + fl - wlo;
-        if (e == 0.f) {
-          acc[q] = win[wpad<LQ>(m)];
-        } else {
-          const float s_e = sinpif(e) * kInvPi;
-          for (int k = -HALF + 1; k <= HALF; ++k) {
-            const float h = tap_weight(a, e, s_e, k);
-            const float2 v = win[wpad<LQ>(m + k)];
-            acc[q].x = fmaf(v.x, h, acc[q].x);
-            acc[q].y = fmaf(v.y, h, acc[q].y);
-          }
+    for (int q = 0; q < Q; ++q) {
+      const int i = ow + lane * Q + q;
+      int fl;
+      float e;
+      rs_delay(I.dl_hi, I.dl_lo, (float)i, fl, e);
+      const int base = (i - ow) + (fl - fmin) + HALF - 1;   // slice position of tap k = 0
+      if (e == 0.f) {
+        acc[q] = ww[wpad<LQ>(base)];
+      } else {
+        const float s_e = sinpif(e) * kInvPi;
+        for (int k = -HALF + 1; k <= HALF; ++k) {
+          const float h = tap_weight(a, e, s_e, k);
+          const float2 v = ww[wpad<LQ>(base + k)];
+          acc[q].x = fmaf(v.x, h, acc[q].x);
+          acc[q].y = fmaf(v.y, h, acc[q].y);
         }
       }
     }
   }
-  // Output tile through shared memory, then 16-byte coalesced stores.
-  float4* st4 = reinterpret_cast<float4*>(stage) + warp * (W / 2) + lane * (Q / 2);
+  // Stage the warp's W outputs in its slice (16-byte slots, XOR-swizzled so
+  // lanes 4 slots apart use distinct banks), then store them coalesced.
+  __syncwarp();
+  float4* s4 = reinterpret_cast<float4*>(ww);
 #pragma unroll
-  for (int q = 0; q < Q / 2; ++q)
-    st4[q] = make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
-  __syncthreads();
-  const int n_here = min(kRsTile, I.n_out - o0);
-  float2* y = I.y + o0;
+  for (int q = 0; q < Q / 2; ++q) {
+    const int f = lane * (Q / 2) + q;
+    s4[f ^ ((f >> 3) & 7)] = make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
+  }
+  __syncwarp();
+  const int n_here = min(W, I.n_out - ow);
+  float2* y = I.y + ow;
   if ((reinterpret_cast<uintptr_t>(y) & 15) == 0) {
-    const float4* s4 = reinterpret_cast<const float4*>(stage);
-    for (int p = threadIdx.x; 2 * p + 1 < n_here; p += NT)
-      __stcs(reinterpret_cast<float4*>(y) + p, s4[p]);
-    if ((n_here & 1) && threadIdx.x == 0) y[n_here - 1] = stage[n_here - 1];
+    for (int p = lane; 2 * p + 1 < n_here; p += 32)
+      __stcs(reinterpret_cast<float4*>(y) + p, s4[p ^ ((p >> 3) & 7)]);
+    if ((n_here & 1) && lane == 0) {
+      const int p = (n_here - 1) >> 1;
+      const float4 t = s4[p ^ ((p >> 3) & 7)];
+      y[n_here - 1] = make_float2(t.x, t.y);
+    }
   } else {
-    for (int p = threadIdx.x; p < n_here; p += NT) y[p] = stage[p];
+    for (int p = lane; p < n_here; p += 32) {
+      const int f = p >> 1;
+      const float4 t = s4[f ^ ((f >> 3) & 7)];
+      y[p] = (p & 1) ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
+    }
   }
 }
 
