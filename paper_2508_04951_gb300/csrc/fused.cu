@@ -99,14 +99,9 @@ template <int CL> DC_DEV void cluster_sync() {
   if constexpr (CL > 1) cg::this_cluster().sync();
   else __syncthreads();
 }
-// Split cluster barrier: arrive early (relaxed: it only publishes mbarrier
-// initialisation, ordered by fence.mbarrier_init), wait (acquire) just
-// before the first remote access.
+// Wait half of a split cluster barrier (acquire), after an arrive.release.
 template <int CL> DC_DEV void cluster_wait() {
   if constexpr (CL > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-template <int CL> DC_DEV void cluster_arrive_relaxed() {
-  if constexpr (CL > 1) asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
 
 template <int CL> DC_DEV float2* row_of(float2* sm, int owner) {
@@ -299,17 +294,19 @@ cudaError_t launch_one(const FusedArgs& a, cudaStream_t s) {
 // bulk copy, the phase row by coalesced loads; after the inverse row FFT
 // each thread sends its 16 outputs X[n2 = j + 256 r] straight to the CTA
 // that owns column n2 (asynchronous remote stores counted on the owner's
-// receive mbarrier), so no CTA reads another's shared memory and the only
-// cluster barrier is the one that publishes the receive barriers at start.
-// The owner then applies W_L^(-n2 q) from the table and runs its columns.
+// receive mbarrier), so no CTA reads another's shared memory.  The rows are
+// received into the same buffer the row FFT used (one 34 KiB buffer per
+// CTA, 64 registers: 4 CTAs per SM), so one cluster barrier after the row
+// FFTs both frees every buffer and publishes the receive barriers.  The
+// owner then applies W_L^(-n2 q) from the table and runs its columns.
 template <int LOG2L1>
-__global__ void __launch_bounds__(kRowThreads, 3) apply_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
   constexpr int COLS = kRowN / L1;              // columns owned by a CTA
   constexpr int PER = COLS / kRowThreads;       // columns per thread
   extern __shared__ __align__(128) float2 sm[];
-  float2* A = sm;                               // [kRowPitch] row buffer
-  float2* R = sm + kRowPitch;                   // [L1][COLS] received rows (L1 > 1)
+  float2* A = sm;                               // [kRowPitch] row buffer, then
+  float2* R = sm;                               // [L1][COLS] received rows (L1 > 1)
   __shared__ __align__(8) unsigned long long bar_in, bar_r;
 
   const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
@@ -323,7 +320,6 @@ __global__ void __launch_bounds__(kRowThreads, 3) apply_kernel(FusedArgs a) {
     }
   }
   __syncthreads();
-  cluster_arrive_relaxed<L1>();                 // receive barrier published
   if (j == 0) {
     mbar_expect_tx(&bar_in, kRowN * sizeof(float2));
     bulk_g2s(A, I.src + (size_t)k1 * kRowN, kRowN * sizeof(float2), &bar_in);
@@ -345,7 +341,10 @@ __global__ void __launch_bounds__(kRowThreads, 3) apply_kernel(FusedArgs a) {
       if (n < I.n_out) __stcs(I.dst + n, v[r]);
     }
   } else {
-    cluster_wait<L1>();                         // every peer's bar_r is initialised
+    // every peer's row FFT is done with its buffer and its bar_r is
+    // initialised (release/acquire cluster barrier)
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    cluster_wait<L1>();
     const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
     const uint32_t b_loc = smem_addr(&bar_r);
 #pragma unroll
@@ -381,7 +380,7 @@ template <int LOG2L1>
 cudaError_t launch_apply(const FusedArgs& a, cudaStream_t s) {
   constexpr int L1 = 1 << LOG2L1;
   if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float2) * (kRowPitch + (L1 > 1 ? kRowN : 0));
+  const size_t smem = sizeof(float2) * kRowPitch;
   auto k = apply_kernel<LOG2L1>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
