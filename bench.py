@@ -196,6 +196,25 @@ def workload_config(cfg) -> dict:
             "v_r": "U[-8, 8] km/s", "tec": "U[5, 150] TECU", "l2": L2_NOTE, "parallelism": "replicas"}
 
 
+# ------------------------------------------------------- multi-rank timing
+
+def reduce_max_ms(ms: float, dist, device) -> float:
+    """The job's time: the largest of the ranks' timed milliseconds (every rank
+    calls this; without a process group it returns ms)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_msamples_per_s(world: int, samples_per_rank_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank processes its own units (weak
+    scaling), all ranks' samples over the slowest rank's time."""
+    return world * samples_per_rank_step * steps / (max_ms / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
@@ -256,12 +275,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     dcg.dc_profile_enable(ctx, False)
     dcg.dc_check(ctx)
     step_ms = [a.elapsed_time(b) for a, b in events]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_samples * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = reduce_max_ms(sum(step_ms), dist, dev)
+    value = job_msamples_per_s(world, n_samples, args.steps, total_ms)
 
     # ---- dominant kernel roofline (event-timed launches inside the timed region)
     peak, peak_src = load_peaks()
@@ -325,13 +340,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         b.synchronize()
         if k:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = reduce_max_ms(sum(e2e_ms), dist, dev)
     if rank == 0:
-        result["e2e"] = {"value": world * n_samples * len(e2e_ms) / (e2e_total / 1e3) / 1e6,
+        result["e2e"] = {"value": job_msamples_per_s(world, n_samples, len(e2e_ms), e2e_total),
                          "unit": UNIT, "h2d_bytes_per_step": int(x32.nbytes),
                          "d2h_bytes_per_step": int(n_samples * 8), "steps": len(e2e_ms)}
 
