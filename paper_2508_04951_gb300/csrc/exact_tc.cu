@@ -16,7 +16,7 @@
 // sharing each X tile, halving the X traffic per flop) or 128 x 256 for fp16:
 //   warp 0     TMA: X_hi / X_lo tiles (256 columns x 32 samples, 64B swizzle)
 //   warp 1     TMEM allocation (512 columns); one thread issues the MMAs
-//   warps 2-9  generate the S tile (rows x 32) in the same swizzled K-major
+//   warps 2-17 generate the S tile (rows x 32) in the same swizzled K-major
 //              layout, hi and lo, from the Cauchy form
 //              S[n][m] = (-1)^(m + m_n) sin(pi e_n) / (pi ((m_n - m) + e_n)),
 //              a n = m_n + e_n -- one division per element, no table
@@ -41,7 +41,8 @@ constexpr int BN = 256, BK = 32;                     // N columns, K per stage
 constexpr int kHalfRows = 128;                       // rows per MMA (M = 128)
 constexpr int kAPlane = kHalfRows * BK * 2;          // 8 KiB: one 128-row A plane
 constexpr int kBPlane = BN * BK * 2;                 // 16 KiB: one B plane
-constexpr int kThreads = 320;
+constexpr int kProducerWarps = 16;                   // S-tile producers (4 per scheduler)
+constexpr int kThreads = 64 + 32 * kProducerWarps;
 
 // bf16x3: two 128-row halves share every X tile (one accumulator each);
 // fp16x3: one half with two accumulators (hi*hi and the 2^11-scaled cross
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
-      mbar_init(&full_bar[s], 1 + 8);   // TMA arrival + one per producer warp
+      mbar_init(&full_bar[s], 1 + kProducerWarps);   // TMA arrival + one per producer warp
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&acc_bar, 1);
@@ -254,12 +255,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------- S tile producers
-    // bf16: thread -> one of 256 rows, all 4 chunks of 8; fp16: one of 128
-    // rows, 2 of the 4 chunks.
-    constexpr int CHUNKS = FP16 ? 2 : 4;
-    const int p = threadIdx.x - 64;            // 0..255
-    const int nl = FP16 ? (p & 127) : p;
-    const int cbase = FP16 ? (p >> 7) * 2 : 0;
+    // thread -> one of the BM rows and CHUNKS of its 4 chunks of 8 (bf16:
+    // 256 rows, 2 chunks; fp16: 128 rows, 1 chunk)
+    constexpr int NP = 32 * kProducerWarps;
+    constexpr int CHUNKS = 4 * C::BM / NP;
+    static_assert(CHUNKS >= 1 && 4 * C::BM == CHUNKS * NP, "producers cover the tile");
+    const int p = threadIdx.x - 64;            // 0..NP-1
+    const int nl = p % C::BM;
+    const int cbase = (p / C::BM) * CHUNKS;
     const int h = nl >> 7, r = nl & 127;       // half and row inside it
     const int mn = s_m[nl];
     const float en = s_e[nl], sg = s_sig[nl];
