@@ -325,7 +325,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "pairs_timed": len(plain_ms),
             "what": "one (v_r, TEC) pair per call: doppler_resample + iono_correct launches"}
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: the pulse copied
+    # in from pinned memory, the corrected samples stored by the kernels
+    # straight into a pinned host buffer (correct_bank's output may be
+    # page-locked host memory), i.e. read back while the bank runs
     k_e2e = max(1, min(args.steps, args.e2e_steps))
     xh = torch.from_numpy(x32).pin_memory()
     oh = torch.empty(n_samples, dtype=torch.complex64, pin_memory=True)
@@ -334,8 +337,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         xd.copy_(xh, non_blocking=True)
-        step()
-        oh.copy_(out, non_blocking=True)
+        dcg.correct_bank(ctx, xd, v, tec, oh, cfg.fs, cfg.fc)
         b.record(stream)
         b.synchronize()
         if k:
@@ -344,7 +346,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     if rank == 0:
         result["e2e"] = {"value": job_msamples_per_s(world, n_samples, len(e2e_ms), e2e_total),
                          "unit": UNIT, "h2d_bytes_per_step": int(x32.nbytes),
-                         "d2h_bytes_per_step": int(n_samples * 8), "steps": len(e2e_ms)}
+                         "d2h_bytes_per_step": int(n_samples * 8), "steps": len(e2e_ms),
+                         "how": "pulse copied in from pinned memory; results stored by the "
+                                "kernels into a pinned host buffer"}
 
     # ---- CPU baseline: the oracle on a bounded sample, and the error of the
     # GPU result on that sample (rank 0, N = 1 only)

@@ -192,6 +192,10 @@ DC_API dc_status correct_batch(dc_ctx* ctx, const dc_c64* in_dev, dc_c64* out_de
 /* Doppler bank: one pulse corrected for every (v_r, TEC) pair.
  * x_dev: [n]; v_r: host [n_v]; tec_tecu: host [n_tec];
  * out_dev: [n_v][n_tec][n_out] (n_out = opts->n_out or n).  Windowed mode only.
+ *          out_dev is written once and never read, so it may also be
+ *          page-locked host memory (cudaHostAlloc / cudaHostRegister): the
+ *          inverse-transform kernel then stores the results straight into
+ *          it over the host link, overlapping the transfer with the work.
  * Resampling and the forward transform run once per v_r, the phase multiply
  * and inverse transform once per pair. */
 DC_API dc_status correct_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n, const double* v_r,

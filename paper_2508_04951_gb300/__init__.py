@@ -126,12 +126,14 @@ def exported_symbols() -> list[str]:
 
 # ---------------------------------------------------------------- helpers
 
-def _ptr(t) -> int:
+def _ptr(t, pinned_ok: bool = False) -> int:
+    """Device address of a contiguous complex64 tensor: a CUDA tensor, or
+    (pinned_ok) a page-locked host tensor, which the GPU addresses directly."""
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch tensor")
-    if not t.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+    if not t.is_cuda and not (pinned_ok and t.is_pinned()):
+        raise ValueError("expected a CUDA tensor" + (" or a pinned host tensor" if pinned_ok else ""))
     if t.dtype != torch.complex64:
         raise TypeError(f"expected complex64, got {t.dtype}")
     if not t.is_contiguous():
@@ -262,7 +264,8 @@ def correct_bank(ctx: Context, x, v_r, tec_tecu, out, fs: float, fc: float, *, t
     t = np.ascontiguousarray(np.asarray(tec_tecu, dtype=np.float64))
     o = _opts(taps, beta, DC_WINDOWED, n_out)
     ctx.check(ctx.lib.correct_bank(ctx.handle, _ptr(x), x.numel(), _dptr(v), len(v), _dptr(t),
-                                   len(t), _ptr(out), fs, fc, ctypes.byref(o), _stream(stream)))
+                                   len(t), _ptr(out, pinned_ok=True), fs, fc, ctypes.byref(o),
+                                   _stream(stream)))
 
 
 def resample_exact_batch(ctx: Context, x, n: int, n_pulses: int, v_r, y, *, n_out=0,
@@ -317,7 +320,7 @@ def dc_plan_bank(ctx: Context, x, v_r, tec_tecu, out, fs: float, fc: float, *, t
     o = _opts(taps, beta, DC_WINDOWED, n_out)
     h = ctypes.c_void_p()
     ctx.check(ctx.lib.dc_plan_bank(ctx.handle, _ptr(x), x.numel(), _dptr(v), len(v), _dptr(t), len(t),
-                                   _ptr(out), fs, fc, ctypes.byref(o), ctypes.byref(h)))
+                                   _ptr(out, pinned_ok=True), fs, fc, ctypes.byref(o), ctypes.byref(h)))
     return Plan(ctx, h, (x, out, v, t))
 
 

@@ -289,6 +289,27 @@ def test_correct_bank_matches_oracle(dcg, ctx, n, n_v, n_tec):
             assert rel(out[i, t], ref[i, t]) <= TOL
 
 
+def test_correct_bank_into_pinned_host_memory(dcg, ctx):
+    # correct_bank's output may be page-locked host memory (the kernels store
+    # into it directly): identical to the device result, bit for bit
+    import torch
+    n, n_v, n_tec = 65536, 3, 4
+    x = noise(n, salt=3)
+    v = np.linspace(-7000, 6000, n_v)
+    tec = np.linspace(10, 140, n_tec)
+    xd = to_dev(x)
+    od = torch.empty(n_v * n_tec * n, dtype=torch.complex64, device="cuda:0")
+    oh = torch.empty(n_v * n_tec * n, dtype=torch.complex64, pin_memory=True)
+    dcg.correct_bank(ctx, xd, v, tec, od, 20e6, 1e9)
+    dcg.correct_bank(ctx, xd, v, tec, oh, 20e6, 1e9)
+    torch.cuda.synchronize()
+    dcg.dc_check(ctx)
+    assert torch.equal(od.cpu(), oh)
+    with pytest.raises(ValueError):
+        dcg.correct_bank(ctx, xd, v, tec, torch.empty(n_v * n_tec * n, dtype=torch.complex64),
+                         20e6, 1e9)                                       # pageable: refused
+
+
 def test_correct_bank_full_size_sampled(dcg, ctx):
     # The Doppler-bank workload at full size, in the launch configuration the
     # benchmark times; sampled (v_r, TEC) pairs checked whole against the oracle.
