@@ -244,6 +244,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     def step():
         dcg.correct_bank(ctx, xd, v, tec, out, cfg.fs, cfg.fc)
 
+    schedule = None
+    if args.autotune:
+        schedule = dcg.dc_autotune_bank(ctx, xd, v, tec, out, cfg.fs, cfg.fc)
     for _ in range(args.warmup):
         step()
     dcg.dc_check(ctx)
@@ -301,6 +304,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                            "p99": float(np.percentile(step_ms, 99))},
             "wall_ms_per_step": 1e3 * t_wall / args.steps,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roofline,
+            "schedule": schedule if schedule else "built-in rules (--no-autotune)",
         }
 
     # ---- plain per-pulse path: each (v_r, TEC) pair alone, single-pulse entry points
@@ -503,6 +507,7 @@ def run_batch(args) -> None:
     stream = torch.cuda.current_stream()
     xd = torch.from_numpy(x).cuda()
     od = torch.empty_like(xd)
+    schedule = dcg.dc_autotune_batch(ctx, xd, od, items) if args.autotune else None
     plan = dcg.dc_plan_batch(ctx, xd, od, items)
     for _ in range(args.warmup):
         plan.execute()
@@ -578,6 +583,7 @@ def run_batch(args) -> None:
                    "l2": "flushed between timed steps (256 MiB write outside the step events)"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
         "graph_launches_per_step": plan.launches, "direct_call_ms": direct_ms,
+        "schedule": schedule if schedule else "built-in rules (--no-autotune)",
         "phases_ms_direct": {k: vv[2] for k, vv in prof_direct.items()},
         "clocks": clk,
         "plain_path": {"value": ps / (sum(plain) / 1e3) / 1e6, "unit": UNIT,
@@ -833,6 +839,8 @@ def main() -> None:
                          "replays; split: the exact-sinc tensor-core GEMM; batch: the uneven "
                          "batch; serve: the Poisson request stream")
     ap.add_argument("--replays", type=int, default=10000, help="plain: graph replays per mode")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="bank, batch: measure the schedule choices first (dc_autotune_*)")
     ap.add_argument("--cpu-all-cores", action=argparse.BooleanOptionalAction, default=True,
                     help="bank: also time the oracle on every host core (spawned processes)")
     ap.add_argument("--cpu-per-core-v", type=int, default=4,

@@ -270,6 +270,44 @@ DC_API dc_status dc_serve_stats(dc_server* server, double* p50_s, double* p99_s,
                                 double* msamples_per_s, long long* completed);
 DC_API dc_status dc_serve_stop(dc_server* server);
 
+/* ----------------------------------------------------------- autotuning
+ * Schedule choices of correct_batch / correct_bank (plans record whatever
+ * the context holds when they are created):
+ *   resample_q  outputs per lane of the tiled windowed resampler, 8 or 4
+ *               (8 only applies where its quadratic tap weights hold);
+ *   fft[m]      for L = 2^m, 4096 <= L <= 65536: 1 = cluster-fused kernels,
+ *               2 = one row pass (L = 4096) or three passes;
+ *   chunk[m]    bytes of three-pass intermediate per chunk of transforms of
+ *               L = 2^m (-1 = a whole length class at once).
+ * 0 in any field means the library's built-in rule. */
+typedef struct {
+  int resample_q;
+  int fft[21];
+  long long chunk[21];
+  double ms_default;    /* the tuned call under the schedule held before tuning */
+  double ms_best;       /* the same call under the chosen schedule              */
+  int candidates;       /* schedules timed                                      */
+} dc_tuning;
+
+/* Measure the schedule choices the call meets on its own data (each
+ * candidate run and timed with CUDA events on `stream`, one choice at a time
+ * with the others held), keep the fastest in the context, and leave the
+ * call's outputs as written by the chosen schedule.  Synchronous; arguments
+ * as for correct_batch / correct_bank; not allowed while a plan is being
+ * recorded.  `report` (may be NULL) receives the resulting schedule. */
+DC_API dc_status dc_autotune_batch(dc_ctx* ctx, const dc_c64* in_dev, dc_c64* out_dev,
+                                   const dc_item* items, int n_items, const dc_opts* opts,
+                                   void* stream, dc_tuning* report);
+DC_API dc_status dc_autotune_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n, const double* v_r,
+                                  int n_v, const double* tec_tecu, int n_tec, dc_c64* out_dev,
+                                  double fs, double fc, const dc_opts* opts, void* stream,
+                                  dc_tuning* report);
+
+/* Read the context's schedule, or replace it (NULL: back to the built-in
+ * rules).  dc_tuning_set validates every field (DC_EINVAL). */
+DC_API dc_status dc_tuning_get(const dc_ctx* ctx, dc_tuning* out);
+DC_API dc_status dc_tuning_set(dc_ctx* ctx, const dc_tuning* t);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,12 @@ class DcOpts(ctypes.Structure):
                 ("mode", ctypes.c_int), ("n_out", ctypes.c_longlong)]
 
 
+class DcTuning(ctypes.Structure):
+    _fields_ = [("resample_q", ctypes.c_int), ("fft", ctypes.c_int * 21),
+                ("chunk", ctypes.c_longlong * 21), ("ms_default", ctypes.c_double),
+                ("ms_best", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
 class DcPhaseTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
                 ("samples", ctypes.c_longlong), ("ms", ctypes.c_double)]
@@ -106,6 +112,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "dc_serve_stats": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                ctypes.POINTER(ll)]),
         "dc_serve_stop": (i, [vp]),
+        "dc_autotune_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), vp,
+                                  ctypes.POINTER(DcTuning)]),
+        "dc_autotune_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts), vp,
+                                 ctypes.POINTER(DcTuning)]),
+        "dc_tuning_get": (i, [vp, ctypes.POINTER(DcTuning)]),
+        "dc_tuning_set": (i, [vp, ctypes.POINTER(DcTuning)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -424,3 +436,59 @@ def dc_serve_stop(srv: Server) -> None:
         srv.lib.dc_serve_stop(srv.handle)
         srv.handle = None
         srv._keep.clear()
+
+
+# ----------------------------------------------------------- autotuning
+
+def _tuning_dict(t: DcTuning) -> dict:
+    return {"resample_q": t.resample_q,
+            "fft": {m: t.fft[m] for m in range(21) if t.fft[m]},
+            "chunk": {m: t.chunk[m] for m in range(21) if t.chunk[m]},
+            "ms_default": t.ms_default, "ms_best": t.ms_best, "candidates": t.candidates}
+
+
+def dc_autotune_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_WINDOWED,
+                      stream=None) -> dict:
+    """Time the schedule choices of this correct_batch call on its data and keep
+    the fastest in the context (outputs written); returns the schedule."""
+    it = np.ascontiguousarray(np.asarray(items, dtype=ITEM_DTYPE))
+    o = _opts(taps, beta, mode, 0)
+    t = DcTuning()
+    ctx.check(ctx.lib.dc_autotune_batch(ctx.handle, _ptr(inp), _ptr(out), it.ctypes.data, len(it),
+                                        ctypes.byref(o), _stream(stream), ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def dc_autotune_bank(ctx: Context, x, v_r, tec_tecu, out, fs: float, fc: float, *, taps=32,
+                     beta=8.0, n_out=0, stream=None) -> dict:
+    """As dc_autotune_batch for a correct_bank call."""
+    v = np.ascontiguousarray(v_r, dtype=np.float64)
+    tt = np.ascontiguousarray(tec_tecu, dtype=np.float64)
+    o = _opts(taps, beta, DC_WINDOWED, n_out)
+    t = DcTuning()
+    ctx.check(ctx.lib.dc_autotune_bank(ctx.handle, _ptr(x), x.numel(), _dptr(v), len(v), _dptr(tt),
+                                       len(tt), _ptr(out, pinned_ok=True), fs, fc, ctypes.byref(o),
+                                       _stream(stream), ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def dc_tuning_get(ctx: Context) -> dict:
+    t = DcTuning()
+    ctx.check(ctx.lib.dc_tuning_get(ctx.handle, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def dc_tuning_set(ctx: Context, schedule: dict | None) -> None:
+    """Replace the context's schedule ({"resample_q", "fft": {m: v}, "chunk": {m: bytes}});
+    None restores the built-in rules."""
+    if schedule is None:
+        ctx.check(ctx.lib.dc_tuning_set(ctx.handle, None))
+        return
+    t = DcTuning()
+    t.resample_q = int(schedule.get("resample_q", 0))
+    for m, v in schedule.get("fft", {}).items():
+        t.fft[int(m)] = int(v)
+    for m, v in schedule.get("chunk", {}).items():
+        t.chunk[int(m)] = int(v)
+    ctx.check(ctx.lib.dc_tuning_set(ctx.handle, ctypes.byref(t)))
+

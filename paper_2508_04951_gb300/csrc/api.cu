@@ -58,6 +58,13 @@ struct dc_ctx {
   double acc_ms[16] = {};
   long long acc_launches[16] = {};
   long long acc_samples[16] = {};
+  // Schedule decisions, 0 = the built-in rule; dc_opts.autotune measures
+  // them on a call's own data (see autotune below).
+  struct Tune {
+    int rs_q = 0;              // outputs per lane of the tiled resampler: 8 or 4
+    long long chunk[21] = {};  // three-pass intermediate bytes per chunk (-1: whole class)
+    int fft[21] = {};          // 4096 <= L <= 65536: 1 cluster-fused, 2 three passes
+  } tune;
   std::recursive_mutex mu;
 };
 
@@ -87,6 +94,22 @@ const char* kPhaseName[PH_COUNT] = {"resample_tiled", "resample_direct", "exact_
                                     "exact_tc"};
 // Transform lengths handled by the cluster-fused kernels.
 bool fused_L(int log2L) { return log2L >= 12 && log2L <= 16; }
+
+// The transform schedule of a length class: cluster-fused (4096 <= L <=
+// 65536 unless tuned otherwise), else one row pass (L <= 4096) or three
+// passes over an intermediate processed in chunks.
+bool use_fused(const dc_ctx* c, int log2L) { return fused_L(log2L) && c->tune.fft[log2L] != 2; }
+
+// Transforms per chunk of a three-pass class.  The tuned intermediate size
+// wins; else `dflt` bytes (0: the whole class at once -- the batch, whose
+// passes lose more to small launches than they gain from L2; the bank uses
+// 64 MiB, which also bounds its scratch).
+size_t chunk_items(const dc_ctx* c, int log2L, size_t count, size_t dflt) {
+  const long long cb = c->tune.chunk[log2L] ? c->tune.chunk[log2L] : (long long)dflt;
+  if (cb <= 0) return std::max<size_t>(count, 1);
+  const size_t per = ((size_t)1 << log2L) * sizeof(float2);
+  return std::max<size_t>(1, std::min(count, (size_t)cb / per));
+}
 
 cudaEvent_t take_event(dc_ctx* c) {
   if (!c->pool.empty()) {
@@ -326,7 +349,7 @@ dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, 
   for (auto& it : items) {
     const double dl = std::fabs((double)it.dl_hi + (double)it.dl_lo);
     if (o.taps != 32 || dl > kRsTiledMaxDelta) direct.push_back(it);
-    else (resample_q(dl) == 8 ? tiled8 : tiled4).push_back(it);
+    else (resample_q(dl) == 8 && c->tune.rs_q != 4 ? tiled8 : tiled4).push_back(it);
   }
   for (int pass = 0; pass < 3; ++pass) {
     auto& v = pass == 0 ? tiled8 : pass == 1 ? tiled4 : direct;
@@ -362,11 +385,11 @@ size_t items_bytes_for(size_t n) { return ((n * 128 + 255) & ~(size_t)255) + 163
 // One L class of pulses already resampled into y; writes corrected outputs.
 // Four-step classes use T (L samples per item) from the scratch.
 dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2* T,
-                         size_t& item_at, cudaStream_t s) {
+                         size_t chunk, size_t& item_at, cudaStream_t s) {
   if (it.empty()) return DC_OK;
   const FftItem* dev = nullptr;
   cudaError_t e;
-  if (fused_L(log2L)) {
+  if (use_fused(c, log2L)) {
     dc_status st = upload(c, it, item_at, s, &dev);
     if (st) return st;
     item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
@@ -392,10 +415,11 @@ dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2*
   }
   const int log2L1 = log2L - 12;
   const size_t L = (size_t)1 << log2L;
-  // pass 1: y -> T ; pass 2: T in place ; pass 3: T -> out
+  // pass 1: y -> T ; pass 2: T in place ; pass 3: T -> out, chunk by chunk
+  // (T holds `chunk` transforms)
   std::vector<FftItem> p1 = it, p2 = it, p3 = it;
   for (size_t i = 0; i < it.size(); ++i) {
-    float2* Ti = T + i * L;
+    float2* Ti = T + (i % chunk) * L;
     p1[i].dst = Ti;
     p2[i].src = Ti;
     p2[i].dst = Ti;
@@ -409,23 +433,26 @@ dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2*
   item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
   if ((st = upload(c, p3, item_at, s, &d3))) return st;
   item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
-  long long outs = 0;
-  for (auto& f : it) outs += f.n_out;
-  ColArgs a1{d1, (int)it.size(), log2L, log2L1, c->tw};
-  {
-    Phase ph(c, PH_COL_F1, s, outs);
-    if ((e = launch_col(COL_F1, a1, s)) != cudaSuccess) return cuda_fail(c, e, "col F1 launch");
-  }
-  RowArgs a2{d2, (int)it.size(), log2L, log2L1, c->tw};
-  {
-    Phase ph(c, PH_ROW_MID, s, outs);
-    e = log2L >= 17 ? launch_row_mid_4096(a2, s) : launch_row(ROW_MID, a2, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "row launch");
-  }
-  ColArgs a3{d3, (int)it.size(), log2L, log2L1, c->tw};
-  {
-    Phase ph(c, PH_COL_B, s, outs);
-    if ((e = launch_col(COL_B, a3, s)) != cudaSuccess) return cuda_fail(c, e, "col B launch");
+  for (size_t j0 = 0; j0 < it.size(); j0 += chunk) {
+    const int cnt = (int)std::min(chunk, it.size() - j0);
+    long long outs = 0;
+    for (size_t i = j0; i < j0 + cnt; ++i) outs += it[i].n_out;
+    ColArgs a1{d1 + j0, cnt, log2L, log2L1, c->tw};
+    {
+      Phase ph(c, PH_COL_F1, s, outs);
+      if ((e = launch_col(COL_F1, a1, s)) != cudaSuccess) return cuda_fail(c, e, "col F1 launch");
+    }
+    RowArgs a2{d2 + j0, cnt, log2L, log2L1, c->tw};
+    {
+      Phase ph(c, PH_ROW_MID, s, outs);
+      e = log2L >= 17 ? launch_row_mid_4096(a2, s) : launch_row(ROW_MID, a2, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "row launch");
+    }
+    ColArgs a3{d3 + j0, cnt, log2L, log2L1, c->tw};
+    {
+      Phase ph(c, PH_COL_B, s, outs);
+      if ((e = launch_col(COL_B, a3, s)) != cudaSuccess) return cuda_fail(c, e, "col B launch");
+    }
   }
   return DC_OK;
 }
@@ -632,7 +659,7 @@ dc_status iono_correct(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, doubl
   it[0].n_valid = (int)n;
   it[0].n_out = (int)n;
   size_t at = 0;
-  return run_iono_class(c, it, log2L, reinterpret_cast<float2*>(c->ws), at, S(stream));
+  return run_iono_class(c, it, log2L, reinterpret_cast<float2*>(c->ws), 1, at, S(stream));
 }
 
 dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item* items,
@@ -673,9 +700,12 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
   // Group by L.
   std::vector<std::vector<int>> by_L(21);
   for (int i = 0; i < n_items; ++i) by_L[log2L[i]].push_back(i);
-  std::vector<size_t> class_T(21, 0);
+  std::vector<size_t> class_T(21, 0), class_chunk(21, 1);
   for (int m = 13; m <= 20; ++m)
-    if (!by_L[m].empty()) class_T[m] = ar.take(by_L[m].size() * ((size_t)1 << m) * sizeof(float2));
+    if (!by_L[m].empty() && !use_fused(c, m)) {
+      class_chunk[m] = chunk_items(c, m, by_L[m].size(), 0);
+      class_T[m] = ar.take(class_chunk[m] * ((size_t)1 << m) * sizeof(float2));
+    }
   if ((st = ensure_ws(c, ar.off))) return st;
   if ((st = ensure_items(c, items_bytes_for((size_t)n_items * 4)))) return st;
   char* ws = c->ws;
@@ -726,7 +756,7 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
       fi[j].n_out = no;
     }
     float2* T = reinterpret_cast<float2*>(ws + class_T[m]);
-    if ((st = run_iono_class(c, fi, m, T, item_at, s))) return st;
+    if ((st = run_iono_class(c, fi, m, T, class_chunk[m], item_at, s))) return st;
   }
   return DC_OK;
 }
@@ -776,15 +806,17 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   const int log2L = log2_ceil(n_out);
   const size_t L = (size_t)1 << log2L;
   const bool four = log2L > 12;
+  const bool fused = use_fused(c, log2L);
   // Transforms per chunk of the inverse (four-step T kept small enough to
   // stay in L2 between its two passes).
-  const int chunk = four ? std::max(1, (int)((64ull << 20) / (L * sizeof(float2)))) : n_v * n_tec;
+  const int chunk =
+      four ? (int)chunk_items(c, log2L, (size_t)n_v * n_tec, (size_t)64 << 20) : n_v * n_tec;
   Arena ar;
   const size_t y_at = ar.take((size_t)n_v * n_out * sizeof(float2));
   const size_t p_at = ar.take((size_t)n_tec * L * sizeof(float2));
   const size_t s_at = ar.take((size_t)n_v * L * sizeof(float2));
   const size_t t_at =
-      ar.take(fused_L(log2L) ? 0 : (size_t)std::max(chunk, four ? n_v : 0) * L * sizeof(float2));
+      ar.take(fused ? 0 : (size_t)std::max(chunk, four ? n_v : 0) * L * sizeof(float2));
   if ((st = ensure_ws(c, ar.off))) return st;
   const size_t n_pairs = (size_t)n_v * n_tec;
   if ((st = ensure_items(c, items_bytes_for(n_pairs * 2 + n_v * 6 + n_tec)))) return st;
@@ -806,7 +838,7 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     const size_t total = L * n_tec;
     const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     Phase phs(c, PH_PHASE_TABLE, s, (long long)total);
-    phase_table_kernel<<<grid, 256, 0, s>>>(dph, n_tec, log2L, fused_L(log2L) ? 1 : 0, P);
+    phase_table_kernel<<<grid, 256, 0, s>>>(dph, n_tec, log2L, fused ? 1 : 0, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "phase table launch");
   }
   // 2. resample per v_r
@@ -830,7 +862,6 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     sp[i].n_out = (int)n_out;
   }
   const FftItem* dev = nullptr;
-  const bool fused = fused_L(log2L);
   if (fused) {
     if ((st = upload(c, sp, item_at, s, &dev))) return st;
     item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
@@ -1096,5 +1127,201 @@ extern "C" dc_status dc_plan_destroy(dc_plan* p) {
   if (p->ws) cudaFree(p->ws);
   if (p->items) cudaFree(p->items);
   delete p;
+  return DC_OK;
+}
+
+// ============================================================ autotuning
+// A call's schedule choices measured on its own data: one choice at a time
+// (resampler outputs per lane, then per length class the transform
+// schedule, then the three-pass chunk size), each candidate run once to
+// settle the scratch and then timed (best of three) with CUDA events, kept
+// if it beats the best so far by more than 2 %.
+namespace {
+
+struct Choice {
+  int kind;   // 0 resample_q, 1 fft[m], 2 chunk[m]
+  int m;
+  std::vector<long long> values;
+};
+
+long long tune_get(const dc_ctx* c, const Choice& d) {
+  if (d.kind == 0) return c->tune.rs_q;
+  if (d.kind == 1) return c->tune.fft[d.m];
+  return c->tune.chunk[d.m];
+}
+void tune_set(dc_ctx* c, const Choice& d, long long v) {
+  if (d.kind == 0) c->tune.rs_q = (int)v;
+  else if (d.kind == 1) c->tune.fft[d.m] = (int)v;
+  else c->tune.chunk[d.m] = v;
+}
+
+template <class F>
+dc_status time_call(dc_ctx* c, F& call, cudaStream_t s, double& ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return cuda_fail(c, e, "tuning events");
+  }
+  ms = 1e30;
+  dc_status st = DC_OK;
+  for (int r = 0; r < 3 && !st; ++r) {
+    cudaEventRecord(a, s);
+    st = call();
+    cudaEventRecord(b, s);
+    if (!st && (e = cudaEventSynchronize(b)) != cudaSuccess) st = cuda_fail(c, e, "tuning run");
+    float t = 0.f;
+    if (!st && cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms = std::min(ms, (double)t);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return st;
+}
+
+void tuning_out(const dc_ctx* c, dc_tuning* t) {
+  *t = dc_tuning{};
+  t->resample_q = c->tune.rs_q;
+  for (int m = 0; m <= 20; ++m) {
+    t->fft[m] = c->tune.fft[m];
+    t->chunk[m] = c->tune.chunk[m];
+  }
+}
+
+template <class F>
+dc_status autotune(dc_ctx* c, F&& call, std::vector<Choice> choices, cudaStream_t s,
+                   dc_tuning* report) {
+  if (c->rec) return fail(c, DC_EINVAL, "autotuning while a plan is being recorded");
+  dc_status st = call();
+  cudaError_t e;
+  if (!st && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(c, e, "tuning warm-up");
+  double ms_default = 0, best = 0;
+  if (!st) st = time_call(c, call, s, ms_default);
+  best = ms_default;
+  int candidates = 1;
+  for (const Choice& d : choices) {
+    if (st) break;
+    // the three-pass chunk matters only while the class runs three passes
+    if (d.kind == 2 && d.m <= 16 && c->tune.fft[d.m] != 2) continue;
+    const long long keep = tune_get(c, d);
+    long long best_v = keep;
+    for (long long v : d.values) {
+      if (v == keep) continue;
+      tune_set(c, d, v);
+      st = call();                             // settle scratch for this schedule
+      if (!st && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(c, e, "tuning run");
+      double ms = 0;
+      if (!st) st = time_call(c, call, s, ms);
+      if (st) break;
+      ++candidates;
+      if (ms < 0.98 * best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    tune_set(c, d, best_v);
+  }
+  if (!st) st = call();                        // outputs from the chosen schedule
+  if (!st && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(c, e, "tuned run");
+  if (st) return st;
+  if (report) {
+    tuning_out(c, report);
+    report->ms_default = ms_default;
+    report->ms_best = best;
+    report->candidates = candidates;
+  }
+  return DC_OK;
+}
+
+// Choices a correct_batch / correct_bank call meets: per length class m.
+void class_choices(std::vector<Choice>& ch, int m, size_t transforms) {
+  if (m >= 12 && m <= 16) ch.push_back({1, m, {1, 2}});
+  if (m >= 13) {
+    const long long whole = (long long)transforms << (m + 3);
+    std::vector<long long> v{-1};
+    for (long long b : {256ll << 20, 64ll << 20, 16ll << 20})
+      if (b < whole && b >= (8ll << m)) v.push_back(b);
+    if (v.size() > 1) ch.push_back({2, m, v});
+  }
+}
+
+}  // namespace
+
+extern "C" dc_status dc_autotune_batch(dc_ctx* c, const dc_c64* in, dc_c64* out,
+                                       const dc_item* items, int n_items, const dc_opts* opts,
+                                       void* stream, dc_tuning* report) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  if (n_items < 0 || (n_items > 0 && !items)) return fail(c, DC_EINVAL, "bad item list");
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  std::vector<Choice> ch;
+  std::vector<size_t> count(21, 0);
+  bool q8 = false;
+  for (int i = 0; i < n_items; ++i) {
+    const long long no = items[i].n_out ? items[i].n_out : items[i].n;
+    if (no < 1 || no > kMaxN) return fail(c, DC_EINVAL, "item %d: bad length", i);
+    ++count[log2_ceil(no)];
+    if (std::fabs(items[i].v_r) < kC) q8 |= resample_q(std::fabs(alpha_minus_one(items[i].v_r))) == 8;
+  }
+  if (o.mode == DC_WINDOWED && o.taps == 32 && q8) ch.push_back({0, 0, {8, 4}});
+  for (int m = 0; m <= 20; ++m)
+    if (count[m]) class_choices(ch, m, count[m]);
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
+  return autotune(
+      c, [&]() { return correct_batch(c, in, out, items, n_items, &o, s); }, ch, s, report);
+}
+
+extern "C" dc_status dc_autotune_bank(dc_ctx* c, const dc_c64* x, long long n, const double* v_r,
+                                      int n_v, const double* tec, int n_tec, dc_c64* out,
+                                      double fs, double fc, const dc_opts* opts, void* stream,
+                                      dc_tuning* report) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  if (n_v < 1 || n_tec < 1 || !v_r || !tec) return fail(c, DC_EINVAL, "bad bank lists");
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  const long long n_out = o.n_out ? o.n_out : n;
+  if (n_out < 1 || n_out > kMaxN) return fail(c, DC_EINVAL, "bad length");
+  std::vector<Choice> ch;
+  bool q8 = false;
+  for (int i = 0; i < n_v; ++i)
+    if (std::fabs(v_r[i]) < kC) q8 |= resample_q(std::fabs(alpha_minus_one(v_r[i]))) == 8;
+  if (o.taps == 32 && q8) ch.push_back({0, 0, {8, 4}});
+  class_choices(ch, log2_ceil(n_out), (size_t)n_v * n_tec);
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
+  return autotune(
+      c, [&]() { return correct_bank(c, x, n, v_r, n_v, tec, n_tec, out, fs, fc, &o, s); }, ch, s,
+      report);
+}
+
+extern "C" dc_status dc_tuning_get(const dc_ctx* c, dc_tuning* out) {
+  if (!c || !out) return DC_EINVAL;
+  tuning_out(c, out);
+  return DC_OK;
+}
+
+extern "C" dc_status dc_tuning_set(dc_ctx* c, const dc_tuning* t) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  if (!t) {
+    c->tune = dc_ctx::Tune{};
+    return DC_OK;
+  }
+  if (t->resample_q != 0 && t->resample_q != 4 && t->resample_q != 8)
+    return fail(c, DC_EINVAL, "resample_q must be 0, 4 or 8");
+  for (int m = 0; m <= 20; ++m) {
+    if (t->fft[m] < 0 || t->fft[m] > 2 || (t->fft[m] && (m < 12 || m > 16)))
+      return fail(c, DC_EINVAL, "fft[%d] must be 0, 1 or 2 (and 0 outside 4096 <= L <= 65536)", m);
+    if (t->chunk[m] < -1) return fail(c, DC_EINVAL, "chunk[%d] must be >= -1", m);
+  }
+  c->tune.rs_q = t->resample_q;
+  for (int m = 0; m <= 20; ++m) {
+    c->tune.fft[m] = t->fft[m];
+    c->tune.chunk[m] = t->chunk[m];
+  }
   return DC_OK;
 }
