@@ -106,6 +106,13 @@ DC_API const char* dc_last_error(const dc_ctx* ctx);
  * asynchronous CUDA error. */
 DC_API dc_status dc_check(dc_ctx* ctx, void* stream);
 
+/* Failure-detection self-test: queues on `stream` one kernel that waits, with
+ * the library's bounded poll, on an mbarrier nothing ever completes.  The
+ * wait runs out (about 2^16 polls), the context's error flag is raised, and
+ * the next dc_check on that stream returns DC_ETIMEOUT; the context stays
+ * usable afterwards.  No GPU fault or hang is involved. */
+DC_API dc_status dc_selftest_wait_timeout(dc_ctx* ctx, void* stream);
+
 /* Kernels launched by this context since creation (-1 for a null context). */
 DC_API long long dc_launch_count(const dc_ctx* ctx);
 

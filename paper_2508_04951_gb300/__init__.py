@@ -90,6 +90,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "dc_destroy": (i, [vp]),
         "dc_last_error": (ctypes.c_char_p, [vp]),
         "dc_check": (i, [vp, vp]),
+        "dc_selftest_wait_timeout": (i, [vp, vp]),
         "dc_launch_count": (ll, [vp]),
         "dc_profile_enable": (i, [vp, i]),
         "dc_profile_read": (i, [vp, ctypes.POINTER(DcPhaseTime), i]),
@@ -212,6 +213,12 @@ def dc_opts_default() -> DcOpts:
 
 def dc_check(ctx: Context, stream=None) -> None:
     ctx.check(ctx.lib.dc_check(ctx.handle, _stream(stream)))
+
+
+def dc_selftest_wait_timeout(ctx: Context, stream=None) -> None:
+    """Queue a kernel whose bounded wait runs out; the next dc_check raises
+    DcError with status DC_ETIMEOUT and the context stays usable."""
+    ctx.check(ctx.lib.dc_selftest_wait_timeout(ctx.handle, _stream(stream)))
 
 
 def dc_launch_count(ctx: Context) -> int:

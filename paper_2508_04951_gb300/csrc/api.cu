@@ -16,6 +16,7 @@
 #include "fused.cuh"
 #include "phase.cuh"
 #include "resample.cuh"
+#include "tma.cuh"
 #include "twiddle_host.h"
 
 using namespace dc;
@@ -459,6 +460,10 @@ dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2*
 
 }  // namespace
 
+namespace dc {
+__global__ void stuck_wait_kernel(int* err, int polls);   // failure-detection self-test
+}
+
 // ==================================================================== ABI
 extern "C" {
 
@@ -582,6 +587,17 @@ int dc_profile_read(dc_ctx* c, dc_phase_time* out, int max) {
     ++n;
   }
   return n;
+}
+
+dc_status dc_selftest_wait_timeout(dc_ctx* c, void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  stuck_wait_kernel<<<1, 32, 0, S(stream)>>>(c->err, 1 << 16);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "self-test launch");
+  ++c->launches;
+  return DC_OK;
 }
 
 dc_status dc_check(dc_ctx* c, void* stream) {
@@ -765,6 +781,18 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
 
 // Phase table for the bank: P[t][k] = exp(-i phi_k(TEC_t)).
 namespace dc {
+// Failure-detection self-test: one thread polls, with the same try-wait and
+// flag the library's bounded waits use, an mbarrier that nothing arrives
+// on; the poll runs out, the flag is raised and the kernel returns.
+__global__ void stuck_wait_kernel(int* err, int polls) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  for (int i = 0; i < polls; ++i)
+    if (mbar_try_wait(&bar, 0)) return;
+  atomicExch(err, 1);
+}
+
 // fused != 0: the layout of the cluster-fused kernels -- element k1*4096 + k2
 // holds bin k1 + L1 k2 (L1 = L/4096) -- with the inverse transform's 1/L folded in.
 __global__ void phase_table_kernel(const PhaseParams* ph, int n_tec, int log2L, int fused,

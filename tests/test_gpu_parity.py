@@ -353,3 +353,22 @@ def test_invalid_arguments_launch_nothing(dcg, ctx):
         dcg.iono_correct(ctx, x, y, 20e6, 1e9, float("nan"))
     dcg.dc_check(ctx)
     assert np.all(y.cpu().numpy() == np.complex64(7 - 7j))
+
+
+# ----------------------------------------------------- failure detection
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(dcg, ctx):
+    # a kernel polls an mbarrier nothing completes with the library's bounded
+    # wait: the poll runs out, dc_check reports DC_ETIMEOUT once, and the
+    # context keeps working
+    dcg.dc_selftest_wait_timeout(ctx)
+    with pytest.raises(dcg.DcError) as ei:
+        dcg.dc_check(ctx)
+    assert ei.value.status == 5                      # DC_ETIMEOUT
+    dcg.dc_check(ctx)                                # flag cleared
+    x = noise(20000, salt=8)
+    xd, yd = to_dev(x), empty(20000)
+    dcg.iono_correct(ctx, xd, yd, 20e6, 1e9, 75.0)
+    dcg.dc_check(ctx)
+    ref = oracle.iono_correct(x.astype(np.complex128), 20e6, 1e9, 75.0)
+    assert rel(host(yd), ref) <= TOL
