@@ -51,7 +51,7 @@ ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
 # one ncu capture (profiles/fused_apply_doppler_bank_32v.md: 233.2 MB for the
 # reduced 32-range-rate launch, scaled by the 8x units of the full launch).
 # Cleared whenever the kernel changes after the capture.
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 8 * 233.211e6}
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": None}
 
 
 def load_peaks() -> tuple[float, str]:

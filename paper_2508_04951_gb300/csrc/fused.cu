@@ -95,6 +95,35 @@ DC_DEV void row4096_1buf(float2 (&v)[16], float2* b, int j, const float2* __rest
   dft16<DIR>(v);
 }
 
+// row4096_1buf, and once every thread has read the buffer for the last time
+// (before the last stage's twiddles and DFT) the cluster barrier is arrived
+// at with release semantics: peers may overwrite the buffer after their wait,
+// while this CTA still finishes its last stage.
+template <int DIR>
+DC_DEV void row4096_1buf_arrive(float2 (&v)[16], float2* b, int j, const float2* __restrict__ tw) {
+  float2 w[4];
+  dft16<DIR>(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b[pad16(16 * j + r)] = v[r];
+  stage2_bases<DIR>(w, tw, j & 15);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
+  apply_powers<16>(v, w);
+  dft16<DIR>(v);
+  const int base = (j >> 4) * 256 + (j & 15);
+  stage3_bases<DIR>(w, tw, j);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b[pad16(base + 16 * r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  apply_powers<16>(v, w);
+  dft16<DIR>(v);
+}
+
 template <int CL> DC_DEV void cluster_sync() {
   if constexpr (CL > 1) cg::this_cluster().sync();
   else __syncthreads();
@@ -332,7 +361,8 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = cmul(A[j + 256 * r], v[r]);
   __syncthreads();                              // the row FFT overwrites A
-  row4096_1buf<+1>(v, A, j, a.tw);
+  if constexpr (L1 == 1) row4096_1buf<+1>(v, A, j, a.tw);
+  else row4096_1buf_arrive<+1>(v, A, j, a.tw);  // arrives at the cluster barrier
 
   if constexpr (L1 == 1) {
 #pragma unroll
@@ -342,8 +372,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
     }
   } else {
     // every peer's row FFT is done with its buffer and its bar_r is
-    // initialised (release/acquire cluster barrier)
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    // initialised (the release arrive is inside the row FFT)
     cluster_wait<L1>();
     const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
     const uint32_t b_loc = smem_addr(&bar_r);
