@@ -138,9 +138,9 @@ template <int CL> DC_DEV float2* row_of(float2* sm, int owner) {
   else return sm;
 }
 
-// One 4096-point row per CTA; clusters of L1 CTAs (16 at L = 65536, beyond
-// the portable 8).  Register caps give 3 resident CTAs per SM for the
-// spectrum kernel, 2 for the full correction (phase evaluation).
+// Full correction (FUSED_FULL): one 4096-point row per CTA; clusters of L1
+// CTAs (16 at L = 65536, beyond the portable 8); 2 resident CTAs per SM
+// (registers: the phase evaluation).
 constexpr int kRowsPerCta = 1;
 
 template <int LOG2L1, int OP>
@@ -207,14 +207,9 @@ __global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 
   }
 
   // ---------------------------------------------------------------- rows
-  // FULL/SPEC: the input sits in A (read above), so the forward row starts in
-  // B; its last exchange is in A, so the inverse row starts in B again.
+  // The input sits in A (read above), so the forward row starts in B; its
+  // last exchange is in A, so the inverse row starts in B again.
   row4096<-1>(v, bufB, bufA, j, a.tw);
-  if constexpr (OP == FUSED_SPEC) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) I.dst[(size_t)k1 * kRowN + j + 256 * r] = v[r];
-    return;
-  }
   // phase of bin k = k1 + L1 k2: regroup through B (free: last read before
   // the forward's second barrier) so each thread owns 16 consecutive k2
   if (I.ph.enabled) {
@@ -317,6 +312,95 @@ cudaError_t launch_one(const FusedArgs& a, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k, a);
 }
 
+
+// Spectra (FUSED_SPEC): one row k1 of the four-step spectrum per CTA, one
+// cluster of L1 CTAs per transform.  Each CTA runs the length-L1 forward
+// DFTs of its 4096 / L1 columns straight from global memory, applies
+// W_L^(n2 k1) and sends element k1 of column n2 to the CTA owning row k1
+// (asynchronous remote stores counted on that CTA's receive mbarrier, so no
+// release fence); the received row is transformed in the same buffer.
+template <int LOG2L1>
+__global__ void __launch_bounds__(kRowThreads, 4) spec_kernel(FusedArgs a) {
+  constexpr int L1 = 1 << LOG2L1;
+  constexpr int COLS = kRowN / L1;              // columns per CTA
+  constexpr int PER = COLS / kRowThreads;       // columns per thread
+  extern __shared__ __align__(128) float2 sm[];
+  float2* A = sm;                               // [kRowPitch] received row, row FFT buffer
+  __shared__ __align__(8) unsigned long long bar_r;
+  const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const FftItem I = a.items[blockIdx.x >> LOG2L1];
+  const int j = threadIdx.x;
+  float2 v[16];
+  if constexpr (L1 == 1) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int n = j + 256 * r;
+      v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+    }
+  } else {
+    if (j == 0) {
+      mbar_init(&bar_r, 1);
+      mbar_expect_tx(&bar_r, kRowN * sizeof(float2));
+    }
+    __syncthreads();
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");   // bar_r published
+    const float2* T = a.t4 + kT4Offset(L1);
+    const uint32_t b_loc = smem_addr(&bar_r);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int n2 = k1 * COLS + j + 256 * p;
+      float2 col[L1];
+#pragma unroll
+      for (int n1 = 0; n1 < L1; ++n1) {
+        const int n = n2 + kRowN * n1;
+        col[n1] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+      }
+      dft<L1, -1>(col);
+      float2 w[4];                              // W_L^(2^b n2), conjugates of the table rows
+#pragma unroll
+      for (int b = 0; b < LOG2L1; ++b) w[b] = conj_if<+1>(__ldg(T + b * kRowN + n2));
+      apply_powers<L1>(col, w);
+      if (p == 0) cluster_wait<L1>();           // every receive barrier is initialised
+      const uint32_t dst = smem_addr(A + pad16(n2));
+#pragma unroll
+      for (int q = 0; q < L1; ++q) st_async_c64(dsmem_map(dst, q), col[q], dsmem_map(b_loc, q));
+    }
+    mbar_wait_cluster_bounded(&bar_r, 0, a.err);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
+    __syncthreads();                            // the row FFT overwrites A
+  }
+  row4096_1buf<-1>(v, A, j, a.tw);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) I.dst[(size_t)k1 * kRowN + j + 256 * r] = v[r];
+}
+
+template <int LOG2L1>
+cudaError_t launch_spec(const FusedArgs& a, cudaStream_t s) {
+  constexpr int L1 = 1 << LOG2L1;
+  if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * kRowPitch;
+  auto k = spec_kernel<LOG2L1>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (L1 > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n_items * L1));
+  cfg.blockDim = dim3(kRowThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = L1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
 
 // Spectrum apply (FUSED_APPLY): one row k1 of the transform per CTA, one
 // cluster of L1 CTAs per transform.  The spectrum row arrives by one 32 KiB
@@ -517,7 +601,15 @@ cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s) {
         default: return cudaErrorInvalidValue;
       }
     case FUSED_FULL: return launch_op<FUSED_FULL>(a, s);
-    case FUSED_SPEC: return launch_op<FUSED_SPEC>(a, s);
+    case FUSED_SPEC:
+      switch (a.log2L) {
+        case 12: return launch_spec<0>(a, s);
+        case 13: return launch_spec<1>(a, s);
+        case 14: return launch_spec<2>(a, s);
+        case 15: return launch_spec<3>(a, s);
+        case 16: return launch_spec<4>(a, s);
+        default: return cudaErrorInvalidValue;
+      }
     default: return cudaErrorInvalidValue;
   }
 }

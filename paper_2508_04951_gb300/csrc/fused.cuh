@@ -15,9 +15,11 @@
 //                 on the owner's mbarrier) -> W_L^(-n2 k1) -> inverse
 //                 columns -> out
 //   FUSED_FULL  : y (zero-padded) -> forward columns (DSMEM scatter) ->
-//                 forward rows -> exp(-i phi_k) / L -> inverse rows ->
-//                 inverse columns -> out (truncated to n_out)
-//   FUSED_SPEC  : y -> forward columns -> forward rows -> spectrum rows
+//                 forward rows -> exp(-i phi_k) / L -> inverse rows pushed
+//                 to the column owners (st.async) -> inverse columns -> out
+//                 (truncated to n_out)
+//   FUSED_SPEC  : y -> forward columns pushed to the row owners (st.async)
+//                 -> forward rows -> spectrum rows
 #pragma once
 
 #include "fft.cuh"
