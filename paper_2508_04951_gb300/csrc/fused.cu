@@ -533,7 +533,7 @@ cudaError_t launch_op(const FusedArgs& a, cudaStream_t s) {
 // row FFT, exp(-i phi_k) at bin k1 + L1 k2, inverse row FFT, four-step
 // twiddle W_L^(-n2 k1) -- in place on the scratch T between the column
 // passes.
-__global__ void __launch_bounds__(kRowThreads, 2) row_mid_kernel(RowArgs a) {
+__global__ void __launch_bounds__(kRowThreads, 4) row_mid_kernel(RowArgs a) {
   extern __shared__ __align__(128) float2 sm[];
   const int L1 = 1 << a.log2L1;
   const int g = blockIdx.x;
@@ -541,15 +541,15 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_mid_kernel(RowArgs a) {
   const FftItem I = a.items[item];
   const int j = threadIdx.x;
   float2* bufA = sm;
-  float2* bufB = sm + kRowPitch;
   const float2* src = I.src + (size_t)k1 * kRowN;
   float2 v[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = src[j + 256 * r];
-  row4096<-1>(v, bufA, bufB, j, a.tw);
+  row4096_1buf<-1>(v, bufA, j, a.tw);
   if (I.ph.enabled) {
-    // phase of bin k = k1 + L1 k2, each thread on 16 consecutive k2 (A is
-    // free: last read before the forward's second barrier)
+    // phase of bin k = k1 + L1 k2, each thread on 16 consecutive k2 (the
+    // forward row's last stage read A at exactly the addresses this thread
+    // writes now, so no barrier is needed first)
 #pragma unroll
     for (int r = 0; r < 16; ++r) bufA[pad16(j + 256 * r)] = v[r];
     __syncthreads();
@@ -562,9 +562,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_mid_kernel(RowArgs a) {
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = bufA[pad16(j + 256 * r)];
-    __syncthreads();                           // the inverse row writes A first
   }
-  row4096<+1>(v, bufA, bufB, j, a.tw);
+  __syncthreads();                             // the inverse row writes A first
+  row4096_1buf<+1>(v, bufA, j, a.tw);
   if (k1) {
     const float2 a_j = tw_big<+1>(a.tw, (uint32_t)(j * k1), a.log2L);
     const int m16 = 16 * L1 - 1, step = 256 >> a.log2L1;
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_mid_kernel(RowArgs a) {
 cudaError_t launch_row_mid_4096(const RowArgs& a, cudaStream_t s) {
   if (a.n_items <= 0) return cudaSuccess;
   if (a.log2L - a.log2L1 != 12 || a.log2L1 < 5 || a.log2L1 > 8) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float2) * 2 * kRowPitch;
+  const size_t smem = sizeof(float2) * kRowPitch;
   cudaError_t e = cudaFuncSetAttribute(row_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   row_mid_kernel<<<(unsigned)(a.n_items << a.log2L1), kRowThreads, smem, s>>>(a);
