@@ -39,38 +39,13 @@ DC_DEV void stage3_bases(float2 (&b)[4], const float2* __restrict__ tw, int j) {
 }
 
 // One 4096-point row, thread j of 256.  In: v[r] = x[j + 256 r].
-// Out: v[r] = X[j + 256 r].  Three radix-16 Stockham stages exchanging
-// through two padded shared-memory buffers (element p at p + p/16): stage 1
-// writes b1, stage 2 reads b1 and writes b2, stage 3 reads b2.  One CTA
-// barrier per exchange; the caller must make sure nobody still reads b1 when
-// this starts.  Every thread of the CTA calls this together.
-template <int DIR>
-DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
-                    const float2* __restrict__ tw) {
-  float2 w[4];
-  dft16<DIR>(v);                                           // Ns = 1
-#pragma unroll
-  for (int r = 0; r < 16; ++r) b1[pad16(16 * j + r)] = v[r];
-  stage2_bases<DIR>(w, tw, j & 15);
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = b1[pad16(j + 256 * r)];
-  apply_powers<16>(v, w);                                  // Ns = 16: W256^(r k)
-  dft16<DIR>(v);
-  const int base = (j >> 4) * 256 + (j & 15);
-#pragma unroll
-  for (int r = 0; r < 16; ++r) b2[pad16(base + 16 * r)] = v[r];
-  stage3_bases<DIR>(w, tw, j);
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = b2[pad16(j + 256 * r)];
-  apply_powers<16>(v, w);                                  // Ns = 256: W4096^(r j)
-  dft16<DIR>(v);
-}
-
-// The same row in one padded buffer: a third CTA barrier (before stage 2's
-// writes) replaces the second buffer.  On return other threads may still be
-// reading b.
+// Out: v[r] = X[j + 256 r].  Three radix-16 Stockham stages with the data in
+// registers, exchanging through one padded shared-memory buffer (element p
+// at p + p/16): a CTA barrier after each exchange's writes and one before
+// the second exchange's writes.  The caller must make sure nobody still
+// reads b when this starts; on
+// return other threads may still be reading b.  Every thread of the CTA
+// calls this together.
 template <int DIR>
 DC_DEV void row4096_1buf(float2 (&v)[16], float2* b, int j, const float2* __restrict__ tw) {
   float2 w[4];
@@ -124,194 +99,10 @@ DC_DEV void row4096_1buf_arrive(float2 (&v)[16], float2* b, int j, const float2*
   dft16<DIR>(v);
 }
 
-template <int CL> DC_DEV void cluster_sync() {
-  if constexpr (CL > 1) cg::this_cluster().sync();
-  else __syncthreads();
-}
 // Wait half of a split cluster barrier (acquire), after an arrive.release.
 template <int CL> DC_DEV void cluster_wait() {
   if constexpr (CL > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-
-template <int CL> DC_DEV float2* row_of(float2* sm, int owner) {
-  if constexpr (CL > 1) return cg::this_cluster().map_shared_rank(sm, owner);
-  else return sm;
-}
-
-// Full correction (FUSED_FULL): one 4096-point row per CTA; clusters of L1
-// CTAs (16 at L = 65536, beyond the portable 8); 2 resident CTAs per SM
-// (registers: the phase evaluation).
-constexpr int kRowsPerCta = 1;
-
-template <int LOG2L1, int OP>
-__global__ void __launch_bounds__(kRowsPerCta * kRowThreads, OP == FUSED_FULL ? 2 : 3)
-    fused_kernel(FusedArgs a) {
-  constexpr int L1 = 1 << LOG2L1;
-  constexpr int ROWS = L1 >= kRowsPerCta ? kRowsPerCta : 1;   // rows per CTA
-  constexpr int CL = L1 / ROWS;              // CTAs per cluster (per transform)
-  constexpr int NT = ROWS * kRowThreads;
-  constexpr int COLS = kRowN / CL;           // columns per CTA in the column passes
-  constexpr int PER = COLS / kRowThreads;    // columns per thread
-  constexpr int LOG2L = 12 + LOG2L1;
-  // [ROWS][2][kRowPitch]: per row, buffers A and B; FULL with L1 > 1 adds
-  // [L1][COLS] for the inverse rows received from the cluster
-  extern __shared__ __align__(128) float2 sm[];
-  static_assert(ROWS == 1, "one row per CTA");
-  __shared__ __align__(8) unsigned long long bar_r;
-
-  const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int item = blockIdx.x / CL;
-  const FftItem I = a.items[item];
-  const int t = threadIdx.x;
-  const int lr = t >> 8, j = t & 255;
-  const int k1 = rank * ROWS + lr;
-  float2* bufA = sm + (2 * lr) * kRowPitch;
-  float2* bufB = bufA + kRowPitch;
-  float2 v[16];
-
-  // ---------------------------------------------------------- input side
-  if constexpr (LOG2L1 == 0) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int n = j + 256 * r;
-      v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
-    }
-  } else {
-    if constexpr (OP == FUSED_FULL) {
-      if (t == 0) {                            // published by the cluster barrier below
-        mbar_init(&bar_r, 1);
-        mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
-      }
-    }
-    // forward columns (length L1) of this CTA's column range, times
-    // W_L^(n2 k1), scattered to the rows' owners
-    for (int c = t; c < COLS; c += NT) {
-      const int n2 = rank * COLS + c;
-      float2 col[L1];
-#pragma unroll
-      for (int n1 = 0; n1 < L1; ++n1) {
-        const int n = n2 + kRowN * n1;
-        col[n1] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
-      }
-      dft<L1, -1>(col);
-      float2 w[4];                             // W_L^(2^b n2), conjugates of the table rows
-#pragma unroll
-      for (int b = 0; b < LOG2L1; ++b) w[b] = conj_if<+1>(__ldg(a.t4 + kT4Offset(L1) + b * kRowN + n2));
-      apply_powers<L1>(col, w);
-#pragma unroll
-      for (int q = 0; q < L1; ++q) row_of<CL>(sm, q / ROWS)[(2 * (q % ROWS)) * kRowPitch + pad16(n2)] = col[q];
-    }
-    cluster_sync<CL>();
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = bufA[pad16(j + 256 * r)];
-  }
-
-  // ---------------------------------------------------------------- rows
-  // The input sits in A (read above), so the forward row starts in B; its
-  // last exchange is in A, so the inverse row starts in B again.
-  row4096<-1>(v, bufB, bufA, j, a.tw);
-  // phase of bin k = k1 + L1 k2: regroup through B (free: last read before
-  // the forward's second barrier) so each thread owns 16 consecutive k2
-  if (I.ph.enabled) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) bufB[pad16(j + 256 * r)] = v[r];
-    __syncthreads();
-    float2 u[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) u[i] = bufB[pad16(16 * j + i)];
-    iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) bufB[pad16(16 * j + i)] = u[i];
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = bufB[pad16(j + 256 * r)];
-    __syncthreads();                           // the inverse row writes B first
-  }
-  {
-    const float invL = 1.0f / (float)(1 << LOG2L);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
-  }
-  // B was last read before the forward's second barrier (or just above); A
-  // (read by the forward's stage 3) is next written after the inverse's
-  // first barrier.
-  row4096<+1>(v, bufB, bufA, j, a.tw);
-
-  // ------------------------------------------------------------ output side
-  if constexpr (LOG2L1 == 0) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int n = j + 256 * r;
-      if (n < I.n_out) __stcs(I.dst + n, v[r]);
-    }
-    return;
-  } else {
-    // inverse row outputs X[n2 = j + 256 r] go to the owner of column n2
-    // (asynchronous remote stores counted on its receive barrier); the
-    // owner applies W_L^(-n2 q) and runs its inverse columns
-    float2* R = sm + 2 * kRowPitch;
-    const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
-    const uint32_t b_loc = smem_addr(&bar_r);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int owner = r / PER;
-      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));
-      st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
-    }
-    const float2* T = a.t4 + kT4Offset(L1);
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int c = j + 256 * p;
-      const int n2 = rank * COLS + c;
-      float2 w[4];
-#pragma unroll
-      for (int b = 0; b < LOG2L1; ++b) w[b] = __ldg(T + b * kRowN + n2);   // W_L^(-2^b n2)
-      if (p == 0) mbar_wait_cluster_bounded(&bar_r, 0, a.err);
-      float2 col[L1];
-#pragma unroll
-      for (int q = 0; q < L1; ++q) col[q] = R[q * COLS + c];
-      apply_powers<L1>(col, w);
-      dft<L1, +1>(col);
-#pragma unroll
-      for (int n1 = 0; n1 < L1; ++n1) {
-        const int n = n2 + kRowN * n1;
-        if (n < I.n_out) __stcs(I.dst + n, col[n1]);
-      }
-    }
-  }
-}
-
-template <int LOG2L1, int OP>
-cudaError_t launch_one(const FusedArgs& a, cudaStream_t s) {
-  constexpr int L1 = 1 << LOG2L1;
-  if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
-  constexpr int ROWS = L1 >= kRowsPerCta ? kRowsPerCta : 1;
-  constexpr int CL = L1 / ROWS;
-  constexpr int NT = ROWS * kRowThreads;
-  const size_t smem =
-      sizeof(float2) * (ROWS * 2 * kRowPitch + (OP == FUSED_FULL && L1 > 1 ? kRowN : 0));
-  auto k = fused_kernel<LOG2L1, OP>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (CL > 8) {
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(a.n_items * CL));
-  cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k, a);
-}
-
 
 // Spectra (FUSED_SPEC): one row k1 of the four-step spectrum per CTA, one
 // cluster of L1 CTAs per transform.  Each CTA runs the length-L1 forward
@@ -516,17 +307,161 @@ cudaError_t launch_apply(const FusedArgs& a, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-template <int OP>
-cudaError_t launch_op(const FusedArgs& a, cudaStream_t s) {
-  switch (a.log2L) {
-    case 12: return launch_one<0, OP>(a, s);
-    case 13: return launch_one<1, OP>(a, s);
-    case 14: return launch_one<2, OP>(a, s);
-    case 15: return launch_one<3, OP>(a, s);
-    case 16: return launch_one<4, OP>(a, s);
-    default: return cudaErrorInvalidValue;
+// Full correction (FUSED_FULL): one row k1 of the transform per CTA, one
+// cluster of L1 CTAs per transform, one padded buffer per CTA.  The forward
+// columns run straight from global memory (zero past n_valid), take
+// W_L^(n2 k1) and go to the row owners by asynchronous remote stores; the
+// forward row, exp(-i phi_k) / L at bin k1 + L1 k2 (regrouped so that each
+// thread owns 16 consecutive k2) and the inverse row follow in the same
+// buffer; the inverse row's outputs go to the column owners the same way,
+// which apply W_L^(-n2 q) and run the inverse columns (out truncated to
+// n_out).  One receive mbarrier serves both exchanges (phases 0 and 1).
+template <int LOG2L1>
+__global__ void __launch_bounds__(kRowThreads, 4) full_kernel(FusedArgs a) {
+  constexpr int L1 = 1 << LOG2L1;
+  constexpr int COLS = kRowN / L1;              // columns owned by a CTA
+  constexpr int PER = COLS / kRowThreads;       // columns per thread
+  constexpr int LOG2L = 12 + LOG2L1;
+  extern __shared__ __align__(128) float2 sm[];
+  float2* A = sm;                               // [kRowPitch] received row, row FFTs,
+  float2* R = sm;                               // then [L1][COLS] received inverse rows
+  __shared__ __align__(8) unsigned long long bar_r;
+  const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const FftItem I = a.items[blockIdx.x >> LOG2L1];
+  const int j = threadIdx.x;
+  float2 v[16];
+  if constexpr (L1 == 1) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int n = j + 256 * r;
+      v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+    }
+  } else {
+    if (j == 0) {
+      mbar_init(&bar_r, 1);
+      mbar_expect_tx(&bar_r, kRowN * sizeof(float2));
+    }
+    __syncthreads();
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");   // bar_r published
+    const float2* T = a.t4 + kT4Offset(L1);
+    const uint32_t b_loc = smem_addr(&bar_r);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int n2 = k1 * COLS + j + 256 * p;
+      float2 col[L1];
+#pragma unroll
+      for (int n1 = 0; n1 < L1; ++n1) {
+        const int n = n2 + kRowN * n1;
+        col[n1] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+      }
+      dft<L1, -1>(col);
+      float2 w[4];                              // W_L^(2^b n2), conjugates of the table rows
+#pragma unroll
+      for (int b = 0; b < LOG2L1; ++b) w[b] = conj_if<+1>(__ldg(T + b * kRowN + n2));
+      apply_powers<L1>(col, w);
+      if (p == 0) cluster_wait<L1>();           // every receive barrier is initialised
+      const uint32_t dst = smem_addr(A + pad16(n2));
+#pragma unroll
+      for (int q = 0; q < L1; ++q) st_async_c64(dsmem_map(dst, q), col[q], dsmem_map(b_loc, q));
+    }
+    mbar_wait_cluster_bounded(&bar_r, 0, a.err);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
+    __syncthreads();                            // the row FFT overwrites A
+  }
+  row4096_1buf<-1>(v, A, j, a.tw);
+  if (I.ph.enabled) {
+    // the forward row's last stage read A at exactly the addresses this
+    // thread writes first, so no barrier is needed before the regroup
+#pragma unroll
+    for (int r = 0; r < 16; ++r) A[pad16(j + 256 * r)] = v[r];
+    __syncthreads();
+    float2 u[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
+    iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
+  }
+  {
+    const float invL = 1.0f / (float)(1 << LOG2L);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
+  }
+  __syncthreads();                              // the inverse row writes A first
+  if constexpr (L1 == 1) {
+    row4096_1buf<+1>(v, A, j, a.tw);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int n = j + 256 * r;
+      if (n < I.n_out) __stcs(I.dst + n, v[r]);
+    }
+  } else {
+    // phase 1 of bar_r: the inverse rows (phase 0 has completed above)
+    if (j == 0) mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
+    row4096_1buf_arrive<+1>(v, A, j, a.tw);     // arrives at the cluster barrier
+    cluster_wait<L1>();                         // every peer's buffer is free, bar_r re-armed
+    const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
+    const uint32_t b_loc = smem_addr(&bar_r);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int owner = r / PER;                // n2 = j + 256 r -> owner n2 / COLS
+      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));
+      st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
+    }
+    const float2* T = a.t4 + kT4Offset(L1);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int c = j + 256 * p;
+      const int n2 = k1 * COLS + c;
+      float2 w[4];
+#pragma unroll
+      for (int b = 0; b < LOG2L1; ++b) w[b] = __ldg(T + b * kRowN + n2);   // W_L^(-2^b n2)
+      if (p == 0) mbar_wait_cluster_bounded(&bar_r, 1, a.err);
+      float2 col[L1];
+#pragma unroll
+      for (int q = 0; q < L1; ++q) col[q] = R[q * COLS + c];
+      apply_powers<L1>(col, w);
+      dft<L1, +1>(col);
+#pragma unroll
+      for (int n1 = 0; n1 < L1; ++n1) {
+        const int n = n2 + kRowN * n1;
+        if (n < I.n_out) __stcs(I.dst + n, col[n1]);
+      }
+    }
   }
 }
+
+template <int LOG2L1>
+cudaError_t launch_full(const FusedArgs& a, cudaStream_t s) {
+  constexpr int L1 = 1 << LOG2L1;
+  if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * kRowPitch;
+  auto k = full_kernel<LOG2L1>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (L1 > 8) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n_items * L1));
+  cfg.blockDim = dim3(kRowThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = L1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 
 // Middle pass of the three-pass four-step path for 65536 < L <= 2^20
 // (L1 = L / 4096 in 32..256 rows): one 4096-point row per CTA -- forward
@@ -600,7 +535,15 @@ cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s) {
         case 16: return launch_apply<4>(a, s);
         default: return cudaErrorInvalidValue;
       }
-    case FUSED_FULL: return launch_op<FUSED_FULL>(a, s);
+    case FUSED_FULL:
+      switch (a.log2L) {
+        case 12: return launch_full<0>(a, s);
+        case 13: return launch_full<1>(a, s);
+        case 14: return launch_full<2>(a, s);
+        case 15: return launch_full<3>(a, s);
+        case 16: return launch_full<4>(a, s);
+        default: return cudaErrorInvalidValue;
+      }
     case FUSED_SPEC:
       switch (a.log2L) {
         case 12: return launch_spec<0>(a, s);

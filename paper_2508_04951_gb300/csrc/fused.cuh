@@ -14,10 +14,11 @@
 //                 asynchronous remote stores (st.async, completion counted
 //                 on the owner's mbarrier) -> W_L^(-n2 k1) -> inverse
 //                 columns -> out
-//   FUSED_FULL  : y (zero-padded) -> forward columns (DSMEM scatter) ->
-//                 forward rows -> exp(-i phi_k) / L -> inverse rows pushed
-//                 to the column owners (st.async) -> inverse columns -> out
-//                 (truncated to n_out)
+//   FUSED_FULL  : y (zero-padded) -> forward columns pushed to the row
+//                 owners (st.async) -> forward rows -> exp(-i phi_k) / L ->
+//                 inverse rows pushed to the column owners (st.async) ->
+//                 inverse columns -> out (truncated to n_out); one padded
+//                 row buffer per CTA
 //   FUSED_SPEC  : y -> forward columns pushed to the row owners (st.async)
 //                 -> forward rows -> spectrum rows
 #pragma once
