@@ -39,6 +39,36 @@ DC_DEV void stage3_bases(float2 (&b)[4], const float2* __restrict__ tw, int j) {
 }
 
 // One 4096-point row, thread j of 256.  In: v[r] = x[j + 256 r].
+// Out: v[r] = X[j + 256 r].  Three radix-16 Stockham stages exchanging
+// through two padded shared-memory buffers (element p at p + p/16): stage 1
+// writes b1, stage 2 reads b1 and writes b2, stage 3 reads b2.  One CTA
+// barrier per exchange; the caller must make sure nobody still reads b1 when
+// this starts.  Every thread of the CTA calls this together.
+template <int DIR>
+DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
+                    const float2* __restrict__ tw) {
+  float2 w[4];
+  dft16<DIR>(v);                                           // Ns = 1
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b1[pad16(16 * j + r)] = v[r];
+  stage2_bases<DIR>(w, tw, j & 15);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b1[pad16(j + 256 * r)];
+  apply_powers<16>(v, w);                                  // Ns = 16: W256^(r k)
+  dft16<DIR>(v);
+  const int base = (j >> 4) * 256 + (j & 15);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b2[pad16(base + 16 * r)] = v[r];
+  stage3_bases<DIR>(w, tw, j);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b2[pad16(j + 256 * r)];
+  apply_powers<16>(v, w);                                  // Ns = 256: W4096^(r j)
+  dft16<DIR>(v);
+}
+
+// One 4096-point row, thread j of 256.  In: v[r] = x[j + 256 r].
 // Out: v[r] = X[j + 256 r].  Three radix-16 Stockham stages with the data in
 // registers, exchanging through one padded shared-memory buffer (element p
 // at p + p/16): a CTA barrier after each exchange's writes and one before
@@ -316,8 +346,9 @@ cudaError_t launch_apply(const FusedArgs& a, cudaStream_t s) {
 // buffer; the inverse row's outputs go to the column owners the same way,
 // which apply W_L^(-n2 q) and run the inverse columns (out truncated to
 // n_out).  One receive mbarrier serves both exchanges (phases 0 and 1).
+// At L = 4096 one CTA holds the whole transform and takes two buffers.
 template <int LOG2L1>
-__global__ void __launch_bounds__(kRowThreads, 4) full_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
   constexpr int COLS = kRowN / L1;              // columns owned by a CTA
   constexpr int PER = COLS / kRowThreads;       // columns per thread
@@ -331,10 +362,40 @@ __global__ void __launch_bounds__(kRowThreads, 4) full_kernel(FusedArgs a) {
   const int j = threadIdx.x;
   float2 v[16];
   if constexpr (L1 == 1) {
+    // L = 4096: one CTA, no exchange; two buffers (a second [kRowPitch]
+    // after A) save a CTA barrier per row, which sets this latency path
+    float2* B = sm + kRowPitch;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int n = j + 256 * r;
       v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+    }
+    row4096<-1>(v, A, B, j, a.tw);              // last reads: B after its second barrier
+    if (I.ph.enabled) {
+      // regroup through A (last read before the forward's second barrier)
+#pragma unroll
+      for (int r = 0; r < 16; ++r) A[pad16(j + 256 * r)] = v[r];
+      __syncthreads();
+      float2 u[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
+      iono_apply_run16(I.ph, 16 * j, 1, u);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
+    }
+    const float invL = 1.0f / (float)(1 << LOG2L);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
+    // the inverse row writes first the buffer no thread can still be reading
+    if (I.ph.enabled) row4096<+1>(v, B, A, j, a.tw);
+    else row4096<+1>(v, A, B, j, a.tw);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int n = j + 256 * r;
+      if (n < I.n_out) __stcs(I.dst + n, v[r]);
     }
   } else {
     if (j == 0) {
@@ -368,51 +429,38 @@ __global__ void __launch_bounds__(kRowThreads, 4) full_kernel(FusedArgs a) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
     __syncthreads();                            // the row FFT overwrites A
-  }
-  row4096_1buf<-1>(v, A, j, a.tw);
-  if (I.ph.enabled) {
-    // the forward row's last stage read A at exactly the addresses this
-    // thread writes first, so no barrier is needed before the regroup
+    row4096_1buf<-1>(v, A, j, a.tw);
+    if (I.ph.enabled) {
+      // the forward row's last stage read A at exactly the addresses this
+      // thread writes first, so no barrier is needed before the regroup
 #pragma unroll
-    for (int r = 0; r < 16; ++r) A[pad16(j + 256 * r)] = v[r];
-    __syncthreads();
-    float2 u[16];
+      for (int r = 0; r < 16; ++r) A[pad16(j + 256 * r)] = v[r];
+      __syncthreads();
+      float2 u[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
-    iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
+      for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
+      iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
-    __syncthreads();
+      for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
+      __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
-  }
-  {
+      for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
+    }
     const float invL = 1.0f / (float)(1 << LOG2L);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
-  }
-  __syncthreads();                              // the inverse row writes A first
-  if constexpr (L1 == 1) {
-    row4096_1buf<+1>(v, A, j, a.tw);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int n = j + 256 * r;
-      if (n < I.n_out) __stcs(I.dst + n, v[r]);
-    }
-  } else {
+    __syncthreads();                            // the inverse row writes A first
     // phase 1 of bar_r: the inverse rows (phase 0 has completed above)
     if (j == 0) mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
     row4096_1buf_arrive<+1>(v, A, j, a.tw);     // arrives at the cluster barrier
     cluster_wait<L1>();                         // every peer's buffer is free, bar_r re-armed
     const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
-    const uint32_t b_loc = smem_addr(&bar_r);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int owner = r / PER;                // n2 = j + 256 r -> owner n2 / COLS
       const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));
       st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
     }
-    const float2* T = a.t4 + kT4Offset(L1);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int c = j + 256 * p;
@@ -439,7 +487,7 @@ template <int LOG2L1>
 cudaError_t launch_full(const FusedArgs& a, cudaStream_t s) {
   constexpr int L1 = 1 << LOG2L1;
   if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float2) * kRowPitch;
+  const size_t smem = sizeof(float2) * kRowPitch * (L1 == 1 ? 2 : 1);
   auto k = full_kernel<LOG2L1>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
