@@ -331,6 +331,37 @@ def test_correct_bank_full_size_sampled(dcg, ctx):
     del od
 
 
+def test_correct_batch_full_size_sampled(dcg, ctx):
+    # The uneven-batch workload at full size (4096 ragged pulses, 195.6 M
+    # samples) through the recorded plan the benchmark replays; the shortest,
+    # the longest and random pulses checked whole against the oracle, and
+    # every output finite and written.
+    import torch
+    cfg = synth.UnevenBatch()
+    lens, x, offs, v, tec = cfg.draw()
+    items = np.zeros(cfg.n_pulses, dtype=dcg.ITEM_DTYPE)
+    for i in range(cfg.n_pulses):
+        items[i] = (offs[i], lens[i], offs[i], lens[i], cfg.fs, cfg.fc, v[i], tec[i])
+    xd = torch.from_numpy(x).to("cuda:0")
+    od = empty(len(x))
+    plan = dcg.dc_plan_batch(ctx, xd, od, items)
+    plan.execute()
+    torch.cuda.synchronize()
+    dcg.dc_check(ctx)
+    out = od.cpu().numpy()
+    assert np.all(np.isfinite(out.view(np.float32)))
+    assert not np.any(out == np.complex64(complex(7.0, -7.0)))
+    rng = np.random.default_rng(11)
+    pick = {int(np.argmin(lens)), int(np.argmax(lens))}
+    pick |= set(int(i) for i in rng.choice(cfg.n_pulses, 6, replace=False))
+    for i in sorted(pick):
+        a, n = int(offs[i]), int(lens[i])
+        ref = oracle.correct(x[a:a + n].astype(np.complex128), cfg.fs, cfg.fc, v[i], tec[i])
+        assert rel(out[a:a + n], ref) <= TOL, (i, n)
+    plan.close()
+    del od, xd
+
+
 # ------------------------------------------------------------- validation
 
 def test_invalid_arguments_launch_nothing(dcg, ctx):
