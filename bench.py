@@ -310,24 +310,23 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     # ---- plain per-pulse path: each (v_r, TEC) pair alone, single-pulse entry points
     y_tmp = torch.empty(cfg.n, dtype=torch.complex64, device=dev)
     pairs = [(i % cfg.n_v, (7 * i) % cfg.n_tec) for i in range(args.plain_pairs + 8)]
-    pe = []
-    for j, (i, t) in enumerate(pairs):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def pair_call(k):
+        i, t = pairs[k]
         zslice = out[(i * cfg.n_tec + t) * cfg.n:(i * cfg.n_tec + t + 1) * cfg.n]
-        a.record(stream)
         dcg.doppler_resample(ctx, xd, y_tmp, cfg.fs, cfg.fc, float(v[i]))
         dcg.iono_correct(ctx, y_tmp, zslice, cfg.fs, cfg.fc, float(tec[t]))
-        b.record(stream)
-        if j >= 8:
-            pe.append((a, b))
-    torch.cuda.synchronize()
-    plain_ms = [a.elapsed_time(b) for a, b in pe]
+
+    for k in range(8):
+        pair_call(k)
+    plain_ms = device_times(torch, stream, lambda k: pair_call(8 + k), args.plain_pairs, block=64)
     if rank == 0:
         result["plain_path"] = {
             "value": cfg.n * len(plain_ms) / (sum(plain_ms) / 1e3) / 1e6, "unit": UNIT,
             "p50_ms": float(np.percentile(plain_ms, 50)), "p99_ms": float(np.percentile(plain_ms, 99)),
             "pairs_timed": len(plain_ms),
-            "what": "one (v_r, TEC) pair per call: doppler_resample + iono_correct launches"}
+            "what": "one (v_r, TEC) pair per call: doppler_resample + iono_correct launches, "
+                    "device time with the calls queued ahead of the device"}
 
     # ---- end to end through the C ABI with host buffers: the pulse copied
     # in from pinned memory, the corrected samples stored by the kernels
@@ -545,20 +544,19 @@ def run_batch(args) -> None:
     rng = np.random.default_rng(3)
     pick = rng.choice(cfg.n_pulses, min(args.plain_pairs * 2, cfg.n_pulses), replace=False)
     y_tmp = torch.empty(int(lens.max()), dtype=torch.complex64, device="cuda")
-    pe, ps = [], 0
-    for j, i in enumerate(pick):
+    def pulse_call(k):
+        i = int(pick[k])
         n = int(lens[i])
         xs = xd[offs[i]:offs[i] + n]
         zs = od[offs[i]:offs[i] + n]
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
         dcg.doppler_resample(ctx, xs, y_tmp[:n], cfg.fs, cfg.fc, float(v[i]))
         dcg.iono_correct(ctx, y_tmp[:n], zs, cfg.fs, cfg.fc, float(tec[i]))
-        b.record(stream)
-        pe.append((a, b))
-        ps += n
+
+    for k in range(len(pick)):                          # scratch grown to its largest first
+        pulse_call(k)
     torch.cuda.synchronize()
-    plain = [a.elapsed_time(b) for a, b in pe]
+    plain = device_times(torch, stream, pulse_call, len(pick), block=64)
+    ps = int(sum(int(lens[int(i)]) for i in pick))
     # error on sampled pulses (plan output recomputed)
     plan.execute()
     torch.cuda.synchronize()
@@ -600,13 +598,42 @@ def run_batch(args) -> None:
 
 # ------------------------------------------------------ plain single pulse
 
+def device_times(torch, stream, fn, count: int, block: int = 250):
+    """Device time (ms) of each of `count` calls fn(k), k = 0 .. count-1,
+    each between two events.  A pulse is shorter than the host's time to submit it, so calls
+    issued back to back would leave the device waiting for the host and the
+    events would time the submissions.  Each block of calls is therefore
+    queued behind a bounded device-side sleep (torch's clock-cycle spin) long
+    enough for the whole block to be submitted first; the device then runs
+    the block's calls back to back."""
+    out = []
+    while len(out) < count:
+        nb = min(block, count - len(out))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(nb)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        torch.cuda._sleep(int(2.1e9 * 0.1))             # about 100 ms at the maximum SM clock
+        for k, (a, b) in enumerate(ev):
+            a.record(stream)
+            fn(len(out) + k)
+            b.record(stream)
+        submit_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        if submit_s > 0.08:                             # the sleep did not cover the submissions
+            raise RuntimeError(f"submitting {nb} calls took {submit_s:.3f} s; lower the block size")
+        out += [a.elapsed_time(b) for a, b in ev]
+    return out
+
+
 def run_plain(args) -> None:
     """One LFM pulse (N = 4096, fs = 10 MHz, B = 5 MHz, fc = 1 GHz, v_r = +7.5
     km/s, TEC = 50 TECU) corrected end to end, windowed and exact-sinc: per
     mode a captured plan (one graph launch) replayed --replays times, each
-    replay timed by CUDA events on the device and by the host from submission
-    to completion, against direct entry-point calls (doppler_resample +
-    iono_correct) and the FP64 oracle on one host core."""
+    replay timed by CUDA events on the device (replays queued ahead of the
+    device, see device_times) and by the host from submission to completion,
+    against direct entry-point calls (doppler_resample + iono_correct) timed
+    the same way and the FP64 oracle on one host core."""
     import torch
     import paper_2508_04951_gb300 as dcg
 
@@ -633,15 +660,7 @@ def run_plain(args) -> None:
         for _ in range(max(3, args.warmup)):
             plan.execute()
         dcg.dc_check(ctx)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(R)]
-        torch.cuda.synchronize()
-        for a, b in ev:
-            a.record(stream)
-            plan.execute()
-            b.record(stream)
-        torch.cuda.synchronize()
-        dev_ms = [a.elapsed_time(b) for a, b in ev]
+        dev_ms = device_times(torch, stream, lambda k: plan.execute(), R)
         host_ms = []
         for _ in range(min(R, 2000)):
             t0 = time.perf_counter()
@@ -652,17 +671,12 @@ def run_plain(args) -> None:
         launches = plan.launches
         plan.close()
         # direct calls: two entry points per pulse, no graph
-        pe = []
-        for k in range(min(R, 2000) + 8):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+        def direct_call(k):
             dcg.doppler_resample(ctx, xd, yd, cfg.fs, cfg.fc, cfg.v_r, mode=mode)
             dcg.iono_correct(ctx, yd, od, cfg.fs, cfg.fc, cfg.tec)
-            b.record(stream)
-            if k >= 8:
-                pe.append((a, b))
-        torch.cuda.synchronize()
-        direct = [a.elapsed_time(b) for a, b in pe]
+        for k in range(8):
+            direct_call(k)
+        direct = device_times(torch, stream, direct_call, min(R, 2000), block=100)
         dcg.dc_profile_enable(ctx, True)
         for _ in range(200):
             dcg.doppler_resample(ctx, xd, yd, cfg.fs, cfg.fc, cfg.v_r, mode=mode)

@@ -212,6 +212,50 @@ def test_plain_pulse_config1_both_modes(dcg, ctx):
         assert rel(host(zd), ref) <= TOL, name
 
 
+def test_l4096_pulse_cases(dcg, ctx):
+    # Pulses of 2048 < n_out <= 4096 (L = 4096: one CTA holds the transform)
+    # inside correct_batch: ragged n against n_out, both signs of v_r,
+    # alpha = 1, TEC = 0 (no phase) and the plain config-1 pulse, each
+    # against the oracle; the config-1 pulse also alone and through a
+    # recorded plan, both bitwise equal to its result inside the batch.
+    import torch
+    cfg = synth.PlainPulse()
+    cases = [(3000, 4096, 8000.0, 0.0), (4096, 2100, -7000.0, 120.0), (2049, 2049, 0.0, 50.0),
+             (4096, 4096, 5000.0, 0.0), (cfg.n, cfg.n, cfg.v_r, cfg.tec)]
+    items = np.zeros(len(cases), dtype=dcg.ITEM_DTYPE)
+    xs, off, ooff = [], 0, 0
+    for i, (n, n_out, v, tec) in enumerate(cases):
+        x = cfg.pulse().astype(np.complex64)[:n] if i == len(cases) - 1 else noise(n, salt=300 + i)
+        fs = cfg.fs if i == len(cases) - 1 else 20e6
+        xs.append(x)
+        items[i] = (off, n, ooff, n_out, fs, 1e9, v, tec)
+        off += n
+        ooff += n_out
+    x = np.concatenate(xs)
+    xd, od = to_dev(x), empty(ooff)
+    dcg.correct_batch(ctx, xd, od, items)
+    torch.cuda.synchronize()
+    dcg.dc_check(ctx)
+    out = od.cpu().numpy()
+    for it in items:
+        a, n, o, no = int(it["in_off"]), int(it["n"]), int(it["out_off"]), int(it["n_out"])
+        ref = oracle.correct(x[a:a + n].astype(np.complex128), it["fs"], it["fc"], it["v_r"],
+                             it["tec_tecu"], n_out=no)
+        assert rel(out[o:o + no], ref) <= TOL, (n, no, it["v_r"], it["tec_tecu"])
+    one = items[-1:].copy()
+    one["in_off"] = 0
+    one["out_off"] = 0
+    x1 = to_dev(xs[-1])
+    direct, planned = empty(cfg.n), empty(cfg.n)
+    dcg.correct_batch(ctx, x1, direct, one)
+    plan = dcg.dc_plan_batch(ctx, x1, planned, one)
+    plan.execute()
+    torch.cuda.synchronize()
+    plan.close()
+    assert torch.equal(direct.cpu(), planned.cpu())
+    assert np.array_equal(direct.cpu().numpy(), out[int(items[-1]["out_off"]):])
+
+
 def _ragged_batch(lengths, seed):
     rng = np.random.default_rng(seed)
     items = np.zeros(len(lengths), dtype=__import__("paper_2508_04951_gb300").ITEM_DTYPE)
