@@ -43,15 +43,19 @@ DC_DEV void stage3_bases(float2 (&b)[4], const float2* __restrict__ tw, int j) {
 // through two padded shared-memory buffers (element p at p + p/16): stage 1
 // writes b1, stage 2 reads b1 and writes b2, stage 3 reads b2.  One CTA
 // barrier per exchange; the caller must make sure nobody still reads b1 when
-// this starts.  Every thread of the CTA calls this together.
+// this starts.  Every thread of the CTA calls this together.  f2, f3: the
+// forward transform's stage bases (stage2_bases / stage3_bases with DIR =
+// -1), loaded by the caller ahead of time; the inverse takes their
+// conjugates.
 template <int DIR>
-DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
-                    const float2* __restrict__ tw) {
+DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j, const float2 (&f2)[4],
+                    const float2 (&f3)[4]) {
   float2 w[4];
   dft16<DIR>(v);                                           // Ns = 1
 #pragma unroll
   for (int r = 0; r < 16; ++r) b1[pad16(16 * j + r)] = v[r];
-  stage2_bases<DIR>(w, tw, j & 15);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) w[b] = conj_if<DIR>(f2[b]);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = b1[pad16(j + 256 * r)];
@@ -60,7 +64,8 @@ DC_DEV void row4096(float2 (&v)[16], float2* b1, float2* b2, int j,
   const int base = (j >> 4) * 256 + (j & 15);
 #pragma unroll
   for (int r = 0; r < 16; ++r) b2[pad16(base + 16 * r)] = v[r];
-  stage3_bases<DIR>(w, tw, j);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) w[b] = conj_if<DIR>(f3[b]);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = b2[pad16(j + 256 * r)];
@@ -365,12 +370,17 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
     // L = 4096: one CTA, no exchange; two buffers (a second [kRowPitch]
     // after A) save a CTA barrier per row, which sets this latency path
     float2* B = sm + kRowPitch;
+    // every stage base of both rows loaded up front, beside the input: one
+    // CTA per transform leaves nothing to hide a load issued per stage
+    float2 f2[4], f3[4];
+    stage2_bases<-1>(f2, a.tw, j & 15);
+    stage3_bases<-1>(f3, a.tw, j);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int n = j + 256 * r;
       v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
     }
-    row4096<-1>(v, A, B, j, a.tw);              // last reads: B after its second barrier
+    row4096<-1>(v, A, B, j, f2, f3);            // last reads: B after its second barrier
     if (I.ph.enabled) {
       // regroup through A (last read before the forward's second barrier)
 #pragma unroll
@@ -390,8 +400,8 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
     // the inverse row writes first the buffer no thread can still be reading
-    if (I.ph.enabled) row4096<+1>(v, B, A, j, a.tw);
-    else row4096<+1>(v, A, B, j, a.tw);
+    if (I.ph.enabled) row4096<+1>(v, B, A, j, f2, f3);
+    else row4096<+1>(v, A, B, j, f2, f3);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int n = j + 256 * r;
