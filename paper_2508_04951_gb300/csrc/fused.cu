@@ -19,8 +19,9 @@ DC_DEV int pad16(int p) { return p + (p >> 4); }
 // Stage twiddles of a 4096-point row from the precomputed tables: stage 2
 // multiplies v[r] by W256^(r k), k = j mod 16; stage 3 by W4096^(r j).  Only
 // the table rows r = 1, 2, 4, 8 are read (coalesced across the warp); the
-// other powers are their products (apply_powers).  The bases are loaded
-// ahead of the CTA barrier that precedes their use.
+// other powers are their products (apply_powers).  The one-buffer rows load
+// the bases ahead of the CTA barrier that precedes their use; the two-buffer
+// row of the single-CTA transform takes them loaded at kernel start.
 template <int DIR>
 DC_DEV void stage2_bases(float2 (&b)[4], const float2* __restrict__ tw, int k) {
   const float2* t = tw + kTwS2 + k;             // row r at (r - 1) * 16
