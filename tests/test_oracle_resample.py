@@ -163,6 +163,26 @@ def test_windowed_snr_loss_against_analytic_e5():
     assert pdist.snr_loss_db(ref, y) <= g["loss_db_about"]
 
 
+def test_windowed_error_falls_with_taps_table1():
+    # Table I: the windowed-sinc error against the exact sum shrinks as the
+    # window widens (a trend, not a bound); interior samples of a band-limited
+    # pulse, the same pulse and range rate for every tap count.
+    rng = np.random.default_rng(21)
+    n = 1024
+    X = np.fft.fft(rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    k = np.fft.fftfreq(n)
+    X[np.abs(k) > 0.4] = 0
+    x = np.fft.ifft(X)
+    a = oracle.alpha(6000.0)
+    ref = oracle.resample_exact(x, a, n)
+    inner = slice(200, n - 200)
+    errs = []
+    for taps in (8, 16, 32, 64):
+        y = oracle.resample_windowed(x, a, n, taps=taps)
+        errs.append(np.linalg.norm(y[inner] - ref[inner]) / np.linalg.norm(ref[inner]))
+    assert all(e1 > e2 for e1, e2 in zip(errs, errs[1:])), errs
+
+
 # ----------------------------------------------------------- exact resample
 
 def test_exact_matches_numpy_sinc_matrix():
