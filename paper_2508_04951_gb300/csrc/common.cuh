@@ -26,6 +26,14 @@ template <int DIR> DC_DEV float2 conj_if(float2 w) {
   return DIR < 0 ? w : make_float2(w.x, -w.y);
 }
 
+// (float)i for |i| < 2^22, exactly, on the full-rate integer and FP32 pipes:
+// i added into the mantissa of 1.5 * 2^23 (whose ulp is 1), then 1.5 * 2^23
+// subtracted exactly.  The conversion instruction runs at a quarter of that
+// rate, which matters in loops that convert once per term.
+DC_DEV float exact_i2f(int i) {
+  return __int_as_float(i + 0x4B400000) - 12582912.0f;
+}
+
 // ------------------------------------------------------------ double-float
 // Dekker/Knuth error-free transforms: a value is hi + lo with |lo| <= ulp(hi)/2.
 struct df { float hi, lo; };

@@ -456,6 +456,25 @@ __global__ void __launch_bounds__(256) exact_fp32_kernel(ExArgs a) {
 // call of the single-pulse entry points): one warp per output sample, lanes
 // striding the input, the weight computed once per (n, m) and applied to
 // every pulse, lanes combined by a fixed shuffle tree (deterministic).
+// One lane's share of the sum: terms m = lane, lane + 32, ... (FAST: m_n - m
+// converted by exact_i2f, valid for |m_n - m| < 2^22).
+template <int P, bool FAST>
+DC_DEV void gemv_terms(const float2* __restrict__ x, int n_in, int np, int mn, float e, float sgl,
+                       int lane, float2 (&acc)[P]) {
+  for (int m = lane; m < n_in; m += 32) {
+    const float den = (FAST ? exact_i2f(mn - m) : (float)(mn - m)) + e;
+    const float w = __fdividef(sgl, den);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      if (p < np) {
+        const float2 xv = __ldg(x + (size_t)p * n_in + m);
+        acc[p].x = fmaf(xv.x, w, acc[p].x);
+        acc[p].y = fmaf(xv.y, w, acc[p].y);
+      }
+    }
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) exact_gemv_kernel(ExArgs a) {
   const ExItem& I = a.items[blockIdx.y];
@@ -476,21 +495,14 @@ __global__ void __launch_bounds__(256) exact_gemv_kernel(ExArgs a) {
   }
   const float s = sinpif(e) * kInvPi;
   const float sg = (mn & 1) ? -s : s;
+  const float sgl = (lane & 1) ? -sg : sg;         // (-1)^m: m steps by 32 from lane
   float2 acc[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) acc[p] = make_float2(0.f, 0.f);
-  for (int m = lane; m < a.n_in; m += 32) {
-    const float den = (float)(mn - m) + e;
-    const float w = __fdividef((m & 1) ? -sg : sg, den);
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      if (p < np) {
-        const float2 x = __ldg(I.x + (size_t)p * a.n_in + m);
-        acc[p].x = fmaf(x.x, w, acc[p].x);
-        acc[p].y = fmaf(x.y, w, acc[p].y);
-      }
-    }
-  }
+  // m_n - m lies in (m_n - n_in, m_n]; below 2^22 in size (any Doppler
+  // range rate) it converts exactly without the quarter-rate instruction
+  if (mn < (1 << 22)) gemv_terms<P, true>(I.x, a.n_in, np, mn, e, sgl, lane, acc);
+  else gemv_terms<P, false>(I.x, a.n_in, np, mn, e, sgl, lane, acc);
 #pragma unroll
   for (int p = 0; p < P; ++p) {
 #pragma unroll

@@ -117,6 +117,26 @@ def test_exact_fp32_matches_oracle(dcg, ctx, n, n_out, v):
     assert rel(host(yd), ref) <= TOL
 
 
+def test_exact_fp32_far_positions(dcg, ctx):
+    # alpha = 37/3 (v_r = 0.85 c): alpha n passes 2^22 inside the call, so
+    # the single-pulse kernel's outputs take both of its term loops (exact
+    # integer conversion below 2^22, the plain one above); both against the
+    # oracle, each side of the switch separately.
+    # a white pulse: far from it the sum's alternating signs leave its
+    # Nyquist component, which a band-limited pulse lacks
+    v = 0.85 * 299792458.0
+    n, n_out = 16, 400000
+    rng = np.random.default_rng(12)
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    xd, yd = to_dev(x), empty(n_out)
+    dcg.doppler_resample(ctx, xd, yd, 20e6, 1e9, v, mode=dcg.DC_EXACT_FP32, n_out=n_out)
+    got = host(yd)
+    ref = oracle.resample_exact(x.astype(np.complex128), oracle.alpha(v), n_out)
+    k = int((1 << 22) / oracle.alpha(v))
+    assert rel(got[:k], ref[:k]) <= TOL
+    assert rel(got[k + 2:], ref[k + 2:]) <= TOL
+
+
 @pytest.mark.parametrize("P", [1, 2, 3, 5, 8, 9])
 def test_exact_fp32_few_pulses(dcg, ctx, P):
     # 1..8 pulses per range rate take the warp-per-output kernel, 9 the tiled one;
