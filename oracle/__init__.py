@@ -12,7 +12,9 @@ Techniques for Arbitrary Waveforms Utilizing GPU Compute"):
 
 * ``core``          -- range-rate factor (Eq. 1), time-dilated resampling
                        (Eq. 2) by windowed and exact Whittaker-Shannon
-                       interpolation (Eq. 17, Sec. III-B, Table I), ionospheric
+                       interpolation (Eq. 17, Sec. III-B, Table I) or by
+                       frequency conversion (Sec. I, Table I), the carrier
+                       term of a passband dilation, ionospheric
                        group delay (Eq. 3) and the FFT distortion / correction
                        (Eqs. 15-16).
 * ``predistortion`` -- the comparison waveforms of Sec. II-A/II-C: the Halpin
@@ -37,6 +39,9 @@ from .core import (  # noqa: F401
     resample_windowed,
     resample_exact,
     resample_exact_rows,
+    carrier_term,
+    frequency_conversion,
+    resample,
     fft_length,
     bin_frequencies,
     iono_phase,

@@ -232,12 +232,51 @@ def iono_distort(s, fs: float, fc: float, tec_tecu: float, L: int | None = None)
 
 
 # ---------------------------------------------------------------------------
-# The corrected pulse: Doppler resampling, then ionospheric correction.
+# Carrier term of a passband dilation, and frequency conversion.
 
-def correct(x, fs: float, fc: float, v_r: float, tec_tecu: float,
-            mode: str = "windowed", n_out: int | None = None,
-            taps: int = 32, beta: float = 8.0):
-    """Resample by alpha(v_r) (Eq. 2 via Eq. 17) then apply Eq. 16."""
+def carrier_term(n_out: int, delta: float, fs: float, f: float):
+    """exp(2 pi i f delta n Ts), n = 0 .. n_out-1, delta = alpha - 1.
+
+    A passband signal x(t) exp(2 pi i fc t) dilated by alpha (Eq. 2) is
+    x(alpha t) exp(2 pi i fc alpha t); taken back to baseband about fc it is
+    x(alpha t) times this term with f = fc.  The phase f delta n / fs is
+    formed in cycles and reduced to [-1/2, 1/2] before the exponential."""
+    n = np.arange(int(n_out), dtype=np.float64)
+    cyc = f * delta * n / fs
+    cyc = cyc - np.round(cyc)
+    return np.exp(2j * np.pi * cyc)
+
+
+def frequency_conversion(x, delta: float, fs: float, f_ref: float, n_out: int | None = None):
+    """Frequency conversion (Sec. I method list; Table I): the dilation
+    approximated by a tone multiply, y[n] = x[n] exp(2 pi i f_ref delta n Ts)
+    with x = 0 beyond its N samples.  Exact for a tone at f_ref (whose
+    frequency Eq. 2 scales by alpha); for other frequencies f the tone misses
+    (f - f_ref) delta, so for an LFM the error grows with its bandwidth."""
+    x, single = _as_pulses(x)
+    xs = x[None, :] if single else x
+    n_in = xs.shape[1]
+    n_out = n_in if n_out is None else int(n_out)
+    y = np.zeros((xs.shape[0], n_out), dtype=np.complex128)
+    k = min(n_in, n_out)
+    y[:, :k] = xs[:, :k]
+    y = y * carrier_term(n_out, delta, fs, f_ref)[None, :]
+    return y[0] if single else y
+
+
+def resample(x, fs: float, fc: float, v_r: float, mode: str = "windowed",
+             n_out: int | None = None, taps: int = 32, beta: float = 8.0,
+             carrier_shift: bool = False, freq_ref: float = 0.0):
+    """The Doppler step y[n] = x(alpha n Ts) (Eq. 2) by one of Table I's
+    methods -- "windowed" or "exact" Whittaker-Shannon interpolation (Eq. 17)
+    or "freqconv" (frequency conversion with reference frequency freq_ref).
+    With carrier_shift the samples are baseband about fc and the passband
+    dilation's carrier term carrier_term(.., fc) is applied as well (for
+    "freqconv": a tone at freq_ref + fc)."""
+    dl = alpha_minus_one(v_r)
+    if mode == "freqconv":
+        f = freq_ref + (fc if carrier_shift else 0.0)
+        return frequency_conversion(x, dl, fs, f, n_out)
     a = alpha(v_r)
     if mode == "windowed":
         y = resample_windowed(x, a, n_out, taps, beta)
@@ -245,17 +284,33 @@ def correct(x, fs: float, fc: float, v_r: float, tec_tecu: float,
         y = resample_exact(x, a, n_out)
     else:
         raise ValueError(mode)
+    if carrier_shift:
+        y = y * carrier_term(y.shape[-1], dl, fs, fc)
+    return y
+
+
+# ---------------------------------------------------------------------------
+# The corrected pulse: Doppler resampling, then ionospheric correction.
+
+def correct(x, fs: float, fc: float, v_r: float, tec_tecu: float,
+            mode: str = "windowed", n_out: int | None = None,
+            taps: int = 32, beta: float = 8.0, carrier_shift: bool = False,
+            freq_ref: float = 0.0):
+    """Resample by alpha(v_r) (Eq. 2 via Eq. 17, or frequency conversion)
+    then apply Eq. 16."""
+    y = resample(x, fs, fc, v_r, mode, n_out, taps, beta, carrier_shift, freq_ref)
     return iono_correct(y, fs, fc, tec_tecu)
 
 
 def correct_bank(x, fs: float, fc: float, v_list, tec_list,
-                 n_out: int | None = None, taps: int = 32, beta: float = 8.0):
+                 n_out: int | None = None, taps: int = 32, beta: float = 8.0,
+                 mode: str = "windowed", carrier_shift: bool = False, freq_ref: float = 0.0):
     """One pulse corrected for every (v_r, TEC) pair: out[v][tec][n]."""
     x = np.asarray(x, dtype=np.complex128)
     n_out = x.shape[0] if n_out is None else int(n_out)
     out = np.zeros((len(v_list), len(tec_list), n_out), dtype=np.complex128)
     for iv, v in enumerate(v_list):
-        y = resample_windowed(x, alpha(v), n_out, taps, beta)
+        y = resample(x, fs, fc, v, mode, n_out, taps, beta, carrier_shift, freq_ref)
         for it, tec in enumerate(tec_list):
             out[iv, it] = iono_correct(y, fs, fc, tec)
     return out
