@@ -49,9 +49,9 @@ METRIC = "corrected Msamples/s and p50/p99 pulse latency vs plain path at stated
 UNIT = "Msamples/s"
 ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
 # DRAM bytes (read + write) per launch of the kernel at the full workload, from
-# one ncu capture (profiles/fused_apply_doppler_bank_32v.md: 233.0 MB for the
-# reduced 32-range-rate launch, scaled by the 8x units of the full launch).
-# Cleared whenever the kernel changes after the capture.
+# one ncu capture of the reduced 32-range-rate launch (233.0 MB), scaled by the
+# 8x units of the full launch.  Cleared whenever the kernel changes after the
+# capture.
 TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 8 * 232.981e6}
 
 

@@ -170,11 +170,14 @@ DC_API dc_status iono_correct(dc_ctx* ctx, const dc_c64* x_dev, long long n, dc_
  * The first call on a device sets up that device: it resolves the arrays'
  * device addresses (cudaGetSymbolAddress, with the device current) and writes
  * the twiddle tables with a synchronous copy.  Make that first call before
- * any stream capture.  All calls share the one scratch array and descriptor
- * slots, which keep the last call's contents (the scratch is fully rewritten
- * before it is read, so nothing needs clearing); calls whose work overlaps on
- * the GPU -- on different streams, say -- race with each other, so issue them
- * on one stream or serialise them.  DC_ECUDA on a CUDA runtime error. */
+ * any stream capture.  Each call hands its launch descriptors to the GPU as
+ * kernel parameters (a one-thread kernel stores them into the descriptor
+ * slots), so no host memory is read after the call returns.  All calls share
+ * the one scratch array and descriptor slots, which keep the last call's
+ * contents (the scratch is fully rewritten before it is read, so nothing
+ * needs clearing); calls whose work overlaps on the GPU -- on different
+ * streams, say -- race with each other, so issue them on one stream or
+ * serialise them.  DC_ECUDA on a CUDA runtime error. */
 DC_API dc_status iono_correct_noalloc(const dc_c64* x_dev, long long n, dc_c64* y_dev,
                                       double fs, double fc, double tec_tecu, void* stream);
 

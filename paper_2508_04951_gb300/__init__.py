@@ -258,12 +258,20 @@ def iono_correct_noalloc(x, y, fs: float, fc: float, tec_tecu: float, *, stream=
     callers that may not allocate device memory at run time (fixed-size
     scratch inside the library; n <= 2^18).  Calls that overlap on the GPU
     share that scratch, so keep them on one stream."""
+    import torch
     lib = load()
     n = x.numel()
     if n > NOALLOC_MAX:
         raise DcError(1, f"n = {n} exceeds the {NOALLOC_MAX}-sample static scratch of "
                          "iono_correct_noalloc; use iono_correct with a Context")
-    st = lib.iono_correct_noalloc(_ptr(x), n, _ptr(y), fs, fc, tec_tecu, _stream(stream))
+    xp, yp = _ptr(x), _ptr(y)
+    if y.numel() < n:
+        raise DcError(1, f"output holds {y.numel()} samples, the input {n}")
+    if x.device != y.device:
+        raise DcError(1, f"input on {x.device}, output on {y.device}")
+    # the C entry point runs on the current device: make it the tensors' one
+    with torch.cuda.device(x.device):
+        st = lib.iono_correct_noalloc(xp, n, yp, fs, fc, tec_tecu, _stream(stream))
     if st:
         raise DcError(st, "iono_correct_noalloc rejected its arguments or failed")
 

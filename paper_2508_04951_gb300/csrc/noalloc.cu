@@ -11,7 +11,10 @@
 // the name refers to a host-side shadow).  The first call on a device looks
 // up their device addresses with cudaGetSymbolAddress while that device is
 // current, fills the twiddle tables with a synchronous copy, and caches the
-// addresses per device; later calls reuse them.
+// addresses per device; later calls reuse them.  A call's launch descriptors
+// travel as kernel parameters (by value) into a one-thread kernel that writes
+// them into the descriptor array, so no host memory is read after the call
+// returns.
 #include <cmath>
 #include <mutex>
 
@@ -66,6 +69,16 @@ dc_status prepare(int device, DeviceSlots** out) {
   return DC_OK;
 }
 
+// Writes this call's descriptors into the static descriptor array, which
+// device code of this file may name directly.
+__global__ void set_items_kernel(dc::FftItem a, dc::FftItem b, dc::FftItem c, int count) {
+  g_items[0] = a;
+  if (count > 1) {
+    g_items[1] = b;
+    g_items[2] = c;
+  }
+}
+
 void split(double v, float& hi, float& lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
@@ -116,10 +129,9 @@ extern "C" dc_status iono_correct_noalloc(const dc_c64* x, long long n, dc_c64* 
     host_items[2].src = d->scratch;              // B: scratch -> y
     count = 3;
   }
-  if (cudaMemcpyAsync(d->items, host_items, count * sizeof(dc::FftItem), cudaMemcpyHostToDevice,
-                      s) != cudaSuccess)
-    return DC_ECUDA;
-  cudaError_t e;
+  set_items_kernel<<<1, 1, 0, s>>>(host_items[0], host_items[1], host_items[2], count);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return DC_ECUDA;
   if (log2L <= 12) {
     dc::RowArgs a{d->items, 1, log2L, 0, d->twiddle};
     e = dc::launch_row(dc::ROW_FULL, a, s);

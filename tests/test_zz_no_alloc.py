@@ -1,21 +1,28 @@
 """iono_correct_noalloc: the context-free, allocation-free variant of
-iono_correct for callers that may not allocate device memory while running.
+iono_correct, for callers that may not allocate device memory while they run
+(a receive loop with a fixed memory plan, where cudaMalloc could stall the
+pipeline, or a host whose device memory belongs to its own pool allocator).
 
-Checked through the C ABI against iono_correct (the entry point that uses a
-context and its scratch) on two calls in a row -- the second reuses the
-static scratch the first one left behind -- within the FP32 tolerance of the
-other parity tests.  This file sorts last so that a run stopping at the first
-failure has already run every other test; it also passes alone.
+Checked through the C ABI against the FP64 oracle and against iono_correct
+(the entry point that uses a context and its scratch), on calls made back to
+back -- each later call reuses the static scratch the one before it left
+behind -- within the FP32 tolerance of the other parity tests.  The sizes
+cover every transform schedule this entry point takes: one row pass
+(L <= 4096), and the three passes of the four-step split for L = 2^13
+(length-2 columns) up to 2^18.  This file sorts last so that a run stopping at
+the first failure has already run every other test; it also passes alone.
 """
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
+FS, FC = 20e6, 1e9
 
 
 def rel(a, b):
@@ -31,36 +38,56 @@ def dcg():
 
 
 def _pulse(n, salt):
-    import torch
-    x = synth.bandlimited_noise(n, synth.rng_for(1, salt=salt)).astype(np.complex64)
-    return torch.from_numpy(x).to("cuda:0")
+    return synth.bandlimited_noise(n, synth.rng_for(1, salt=salt)).astype(np.complex64)
 
 
-def test_noalloc_matches_context_path_twice(dcg):
+# n, TEC, seed salt: L = 2^17, 2^12, 2^18, 2^13, 2^16, 2^16 (exactly n = L)
+CASES = ((100000, 120.0, 1), (3000, 40.0, 2), (262144, -60.0, 3), (5000, 150.0, 4),
+         (40000, 75.0, 5), (65536, 10.0, 6))
+
+
+def test_noalloc_matches_oracle_and_context_path(dcg):
     import torch
     ctx = dcg.Context(0)
-    # four-step path (L = 2^17 uses the static scratch), then a single-pass one,
-    # then the four-step path again on a different size.
-    for n, tec, salt in ((100000, 120.0, 1), (3000, 40.0, 2), (262144, -60.0, 3)):
-        x = _pulse(n, salt)
+    for n, tec, salt in CASES:
+        xh = _pulse(n, salt)
+        x = torch.from_numpy(xh).to("cuda:0")
         want = torch.empty_like(x)
-        got = torch.full_like(x, complex(5.0, 5.0))
-        dcg.iono_correct(ctx, x, want, 20e6, 1e9, tec)
-        dcg.iono_correct_noalloc(x, got, 20e6, 1e9, tec)
+        for call in range(2):                   # two calls in a row on the same sizes
+            got = torch.full_like(x, complex(5.0, 5.0))
+            dcg.iono_correct_noalloc(x, got, FS, FC, tec)
+            torch.cuda.synchronize()
+            g = got.cpu().numpy().astype(np.complex128)
+            ref = oracle.iono_correct(xh.astype(np.complex128), FS, FC, tec)
+            assert rel(g, ref) <= TOL, (n, call)
+        dcg.iono_correct(ctx, x, want, FS, FC, tec)
         torch.cuda.synchronize()
-        w = want.cpu().numpy().astype(np.complex128)
-        g = got.cpu().numpy().astype(np.complex128)
-        assert rel(g, w) <= TOL, n
+        assert rel(g, want.cpu().numpy().astype(np.complex128)) <= TOL, n
     ctx.close()
+
+
+def test_noalloc_in_place(dcg):
+    import torch
+    for n, tec, salt in ((5000, 90.0, 7), (200000, 30.0, 8)):
+        xh = _pulse(n, salt)
+        x = torch.from_numpy(xh).to("cuda:0")
+        dcg.iono_correct_noalloc(x, x, FS, FC, tec)   # x is both input and output
+        torch.cuda.synchronize()
+        ref = oracle.iono_correct(xh.astype(np.complex128), FS, FC, tec)
+        assert rel(x.cpu().numpy().astype(np.complex128), ref) <= TOL, n
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(dcg):
     import torch
     x = torch.zeros((1 << 18) + 1, dtype=torch.complex64, device="cuda:0")
     with pytest.raises(dcg.DcError) as e:
-        dcg.iono_correct_noalloc(x, x, 20e6, 1e9, 10.0)
+        dcg.iono_correct_noalloc(x, x, FS, FC, 10.0)
     assert "exceeds" in str(e.value)
     # the C entry point itself refuses too (no launch)
     L = dcg.load()
-    assert L.iono_correct_noalloc(x.data_ptr(), x.numel(), x.data_ptr(), 20e6, 1e9, 10.0,
+    assert L.iono_correct_noalloc(x.data_ptr(), x.numel(), x.data_ptr(), FS, FC, 10.0,
                                   torch.cuda.current_stream().cuda_stream) == 1
+    # an output smaller than the input is refused by the binding
+    small = torch.zeros(100, dtype=torch.complex64, device="cuda:0")
+    with pytest.raises(dcg.DcError):
+        dcg.iono_correct_noalloc(small[:50].contiguous(), small[:10].contiguous(), FS, FC, 1.0)
