@@ -17,6 +17,9 @@ Techniques for Arbitrary Waveforms Utilizing GPU Compute"):
                        term of a passband dilation, ionospheric
                        group delay (Eq. 3) and the FFT distortion / correction
                        (Eqs. 15-16).
+* ``compression``   -- pulse compression bundled with the correction
+                       (Sec. II-B, the pulse-compression path): the corrected
+                       pulse's cross-correlation with a replica.
 * ``predistortion`` -- the comparison waveforms of Sec. II-A/II-C: the Halpin
                        cubic (Eq. 4) and its closed-form root (Eqs. 11-14), the
                        pseudo-Chebyshev expansion (Eqs. 5-10, and the original
