@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .core import C_LIGHT
+from .core import C_LIGHT, KAPPA, TECU
 
 A_CHEB = np.sqrt(3.0) / 2.0        # a = sqrt(3)/2 (Sec. II-A, after Eq. 8)
 
@@ -137,3 +137,33 @@ def snr_loss_db(a, b):
     both (the LFM autocorrelation peak of Fig. 2): -20 log10(peak/(|a||b|))."""
     peak = correlation_peak(a, b)
     return -20.0 * np.log10(peak / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def predistorted_lfm(n: int, fs: float, f0: float, B: float, T: float, tec_tecu: float,
+                     kind: str = "cubic", f_mix: float = 0.0):
+    """The transmit waveforms compared in Sec. II-C, sampled at t_m = m / fs,
+    m = 0 .. n-1, as s[m] = exp(i (phi(t_m) - 2 pi f_mix t_m)):
+
+    * "lfm"   -- the undistorted LFM from f0 over B in T (``lfm_phase``);
+    * "cubic" -- the frequency solving Eq. 4 (Eqs. 11-14), its phase by the
+                 trapezoidal rule (Sec. II-A; the CUBIC waveform of Fig. 2);
+    * "poly"  -- the pseudo-Chebyshev expansion, Eqs. 5-10, phase in closed
+                 form (POLY);
+    * "poly4" -- the same with the original factor-4 coefficients of
+                 Appendix B (Eqs. 23-24), the negative control.
+
+    K2 = kappa E with E = tec_tecu TECU.  f_mix mixes the waveform down
+    (f_mix = 0: RF samples)."""
+    t = np.arange(int(n), dtype=np.float64) / fs
+    K2 = KAPPA * tec_tecu * TECU
+    if kind == "lfm":
+        phi = lfm_phase(t, f0, B, T)
+    elif kind == "cubic":
+        phi = trapezoid_phase(cubic_frequency(t, f0, B, T, K2), 1.0 / fs)
+    elif kind == "poly":
+        phi = chebyshev_phase(t, f0, B, T, K2, 2.0)
+    elif kind == "poly4":
+        phi = chebyshev_phase(t, f0, B, T, K2, 4.0)
+    else:
+        raise ValueError(kind)
+    return np.exp(1j * (phi - 2.0 * np.pi * f_mix * t))

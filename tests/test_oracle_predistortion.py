@@ -120,3 +120,38 @@ def test_e1_negative_controls(e1_waveforms):
     assert pdist.snr_loss_db(w["cubic"], w["fft"](ones, 2 * w["tec"])) > 0.5
     loss4 = pdist.snr_loss_db(w["cubic"], w["poly4"])
     assert 0.5 < loss4 < 3.0 * E7["original_loss_db_about"]
+
+
+def test_generated_waveforms_meet_the_e1_bounds(e1_waveforms):
+    # the sampled transmit waveforms: CUBIC against the FFT-predistorted LFM
+    # and against POLY within Fig. 2's 0.01 dB, the factor-4 POLY about 1 dB
+    # off (Appendix B), and no ionosphere gives the plain LFM back
+    w = e1_waveforms
+    f0, B, fs, T = E1["f0_hz"], E1["bandwidth_hz"], E1["fs_hz"], E1["T_s"]
+    n, tec = w["n"], w["tec"]
+    cubic = pdist.predistorted_lfm(n, fs, f0, B, T, tec, "cubic")
+    assert pdist.snr_loss_db(cubic, w["fft"](np.ones(n), tec)) < E1["max_loss_cubic_vs_fft_db"]
+    assert pdist.snr_loss_db(cubic, pdist.predistorted_lfm(n, fs, f0, B, T, tec, "poly")) < \
+        E1["max_loss_cubic_vs_poly_db"]
+    loss4 = pdist.snr_loss_db(cubic, pdist.predistorted_lfm(n, fs, f0, B, T, tec, "poly4"))
+    assert 0.5 < loss4 < 3.0 * E7["original_loss_db_about"]
+    plain = pdist.predistorted_lfm(n, fs, f0, B, T, tec, "lfm")
+    assert pdist.snr_loss_db(cubic, plain) > 0.5            # the ionosphere matters here
+    # no ionosphere: cubic and poly are the LFM; the trapezoid integrates the
+    # linear frequency exactly, so the cubic one matches to rounding
+    for kind in ("cubic", "poly"):
+        z = pdist.predistorted_lfm(n, fs, f0, B, T, 0.0, kind)
+        assert np.max(np.abs(z - plain)) < 1e-6, kind
+
+
+def test_generated_waveform_mixing():
+    # f_mix moves the spectrum down by f_mix: the baseband waveform times the
+    # mixing tone is the RF one
+    n, fs, f0, B, T = 4096, 2.048e9, 413e6, 18e6, 2e-6
+    rf = pdist.predistorted_lfm(n, fs, f0, B, T, 50.0, "cubic")
+    bb = pdist.predistorted_lfm(n, fs, f0, B, T, 50.0, "cubic", f_mix=f0)
+    t = np.arange(n) / fs
+    np.testing.assert_allclose(bb * np.exp(2j * np.pi * f0 * t), rf, atol=1e-9)
+    # the baseband instantaneous frequency sweeps about 0 .. B
+    inst = np.diff(np.unwrap(np.angle(bb))) * fs / (2 * np.pi)
+    assert -1e6 < inst[0] < 1e6 and abs(inst[-1] - B) < 2e6
