@@ -65,12 +65,19 @@ typedef enum {
   DC_ECANCELLED = 6   /* request cancelled                                  */
 } dc_status;
 
-/* Resampling method (Table I rows "Whittaker-Shannon" and "Windowed"). */
+/* Resampling method (Table I rows "Whittaker-Shannon", "Windowed" and
+ * "Frequency Conversion"). */
 typedef enum {
   DC_WINDOWED = 0,        /* Kaiser-windowed sinc, `taps` taps, FP32        */
   DC_EXACT_FP32 = 1,      /* exact finite sum of Eq. 17, FP32 CUDA cores    */
   DC_EXACT_BF16X3 = 2,    /* exact sum as a tensor-core GEMM, bf16 hi/lo    */
-  DC_EXACT_FP16X3 = 3     /* exact sum as a tensor-core GEMM, fp16 hi/lo    */
+  DC_EXACT_FP16X3 = 3,    /* exact sum as a tensor-core GEMM, fp16 hi/lo    */
+  DC_FREQCONV = 4         /* frequency conversion (Sec. I method list): the
+                             dilation approximated by the tone multiply
+                             y[n] = x[n] exp(2 pi i f (alpha - 1) n Ts),
+                             f = freq_ref (+ fc with carrier_shift), x = 0
+                             past n; exact for a tone at f, error growing as
+                             B^2 for an LFM of bandwidth B (Table I)         */
 } dc_mode;
 
 typedef struct {
@@ -78,11 +85,20 @@ typedef struct {
   double kaiser_beta;   /* Kaiser shape, default 8                           */
   int mode;             /* dc_mode, default DC_WINDOWED                      */
   long long n_out;      /* output samples, 0 = same as input                 */
+  /* 1: the samples are complex baseband about fc and the dilation is that of
+   * the passband signal, so the resampled pulse also takes the carrier term
+   * exp(2 pi i fc (alpha - 1) n Ts) (Eq. 2 applied to x(t) exp(2 pi i fc t),
+   * mixed back down by fc).  0 (default): y[n] = x(alpha n Ts) only.  Not
+   * used by resample_exact_batch.                                           */
+  int carrier_shift;
+  double freq_ref;      /* DC_FREQCONV: frequency (Hz, in the samples' own
+                           frame) at which the tone multiply is exact,
+                           default 0                                         */
 } dc_opts;
 
 typedef struct dc_ctx dc_ctx;
 
-/* Defaults: taps 32, beta 8, DC_WINDOWED, n_out 0. */
+/* Defaults: taps 32, beta 8, DC_WINDOWED, n_out 0, carrier_shift 0, freq_ref 0. */
 DC_API void dc_opts_default(dc_opts* opts);
 
 /* Text of a status code (static storage). */
@@ -136,8 +152,12 @@ DC_API int dc_profile_read(dc_ctx* ctx, dc_phase_time* out, int max);
  * x_dev: [n] input samples.  y_dev: [n_out] output, n_out = opts->n_out or n.
  * Windowed: y[j] = sum_i x[i] h(alpha j - i), h the Kaiser-windowed sinc of
  * half width taps/2, x = 0 outside [0, n).  Exact: y[j] = sum_{i<n} x[i]
- * sinc(alpha j - i).  fs and fc are validated only (the position alpha j is
- * in units of samples).  opts may be NULL (defaults). */
+ * sinc(alpha j - i).  DC_FREQCONV: the tone multiply of dc_mode.  With
+ * opts->carrier_shift the interpolating modes also multiply y[j] by
+ * exp(2 pi i fc (alpha - 1) j / fs).  fs and fc enter only through the
+ * carrier term and frequency conversion (positions are in units of samples).
+ * Modes DC_WINDOWED, DC_EXACT_FP32, DC_FREQCONV.  opts may be NULL
+ * (defaults). */
 DC_API dc_status doppler_resample(dc_ctx* ctx, const dc_c64* x_dev, long long n, dc_c64* y_dev,
                            double fs, double fc, double v_r, const dc_opts* opts,
                            void* stream);
@@ -191,7 +211,8 @@ typedef struct {
 } dc_item;
 
 /* Full correction of a ragged batch: for each item, resample by alpha(v_r)
- * (opts->mode, taps, beta; opts->n_out is ignored, items carry n_out), then
+ * (opts->mode: DC_WINDOWED, DC_EXACT_FP32 or DC_FREQCONV; taps, beta,
+ * carrier_shift, freq_ref; opts->n_out is ignored, items carry n_out), then
  * apply Eq. 16 with its TEC.  in_dev and out_dev hold all items at the given
  * offsets; output ranges must not overlap each other or the inputs.  Each
  * item's result does not depend on the other items of the batch. */
@@ -201,7 +222,8 @@ DC_API dc_status correct_batch(dc_ctx* ctx, const dc_c64* in_dev, dc_c64* out_de
 
 /* Doppler bank: one pulse corrected for every (v_r, TEC) pair.
  * x_dev: [n]; v_r: host [n_v]; tec_tecu: host [n_tec];
- * out_dev: [n_v][n_tec][n_out] (n_out = opts->n_out or n).  Windowed mode only.
+ * out_dev: [n_v][n_tec][n_out] (n_out = opts->n_out or n).  Modes DC_WINDOWED
+ *          and DC_FREQCONV.
  *          out_dev is written once and never read, so it may also be
  *          page-locked host memory (cudaHostAlloc / cudaHostRegister): the
  *          inverse-transform kernel then stores the results straight into
@@ -211,6 +233,38 @@ DC_API dc_status correct_batch(dc_ctx* ctx, const dc_c64* in_dev, dc_c64* out_de
 DC_API dc_status correct_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n, const double* v_r,
                        int n_v, const double* tec_tecu, int n_tec, dc_c64* out_dev,
                        double fs, double fc, const dc_opts* opts, void* stream);
+
+/* Pulse compression bundled with the correction (Sec. II-B, the paragraph
+ * after Eq. 16 and the pulse-compression figure): the frequency-domain pass
+ * of Eq. 16 also applies the matched filter of a replica, so that
+ *
+ *   r = F^-1[ F(y) exp(-i 4 pi K2 / (c f_k)) conj(F(h)) ],  first n_out lags,
+ *
+ * with y the pulse resampled by alpha(v_r) (as correct_batch: opts->mode
+ * DC_WINDOWED, DC_EXACT_FP32 or DC_FREQCONV, carrier_shift, freq_ref;
+ * n_out = opts->n_out or n) zero-padded to L = 2^ceil(log2 n_out), and h the
+ * replica zero-padded to L.  Lag m is sum_j z[(m + j) mod L] conj(h[j]), z the
+ * whole corrected L-buffer: the matched filter's output at delay m, linear
+ * for m <= L - n_rep, circular beyond.
+ * x_dev: [n]; replica_dev: [n_rep], 1 <= n_rep <= L; y_dev: [n_out] lags.
+ * The replica's spectrum is computed on the device in the same call. */
+DC_API dc_status correct_compress(dc_ctx* ctx, const dc_c64* x_dev, long long n,
+                                  const dc_c64* replica_dev, long long n_rep, dc_c64* y_dev,
+                                  double fs, double fc, double v_r, double tec_tecu,
+                                  const dc_opts* opts, void* stream);
+
+/* The Doppler bank (correct_bank) compressed against one replica: out_dev
+ * [n_v][n_tec][n_out] holds, per (v_r, TEC) pair, the lags of
+ * correct_compress.  The replica's spectrum is computed once and its
+ * conjugate folded into each TEC's factor table, so the per-pair
+ * phase-and-inverse pass costs what it costs without compression.  Modes
+ * DC_WINDOWED and DC_FREQCONV; out_dev may be page-locked host memory as for
+ * correct_bank. */
+DC_API dc_status correct_compress_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n,
+                                       const dc_c64* replica_dev, long long n_rep,
+                                       const double* v_r, int n_v, const double* tec_tecu,
+                                       int n_tec, dc_c64* out_dev, double fs, double fc,
+                                       const dc_opts* opts, void* stream);
 
 /* Exact-sinc resampling of many pulses per range rate (Eq. 17 as a dense
  * contraction Y_a = X_a S_a^T, S_a[j][i] = sinc(alpha_a j - i)).

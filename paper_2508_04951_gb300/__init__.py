@@ -21,16 +21,17 @@ from . import build as _build
 
 __all__ = [
     "DcError", "Context", "load", "lib_path",
-    "DC_WINDOWED", "DC_EXACT_FP32", "DC_EXACT_BF16X3", "DC_EXACT_FP16X3",
+    "DC_WINDOWED", "DC_EXACT_FP32", "DC_EXACT_BF16X3", "DC_EXACT_FP16X3", "DC_FREQCONV",
     "ITEM_DTYPE", "dc_opts_default", "dc_check", "dc_launch_count", "dc_profile_enable",
     "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc",
-    "correct_batch", "correct_bank", "resample_exact_batch", "exported_symbols",
+    "correct_batch", "correct_bank", "correct_compress", "correct_compress_bank",
+    "resample_exact_batch", "exported_symbols",
     "Plan", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute", "dc_plan_launches",
     "dc_plan_destroy", "Server", "dc_serve_start", "dc_serve_submit", "dc_serve_wait",
     "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop",
 ]
 
-DC_WINDOWED, DC_EXACT_FP32, DC_EXACT_BF16X3, DC_EXACT_FP16X3 = 0, 1, 2, 3
+DC_WINDOWED, DC_EXACT_FP32, DC_EXACT_BF16X3, DC_EXACT_FP16X3, DC_FREQCONV = 0, 1, 2, 3, 4
 STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_EBUSY", 4: "DC_ECUDA",
           5: "DC_ETIMEOUT", 6: "DC_ECANCELLED"}
 
@@ -41,7 +42,8 @@ ITEM_DTYPE = np.dtype([("in_off", "<i8"), ("n", "<i8"), ("out_off", "<i8"), ("n_
 
 class DcOpts(ctypes.Structure):
     _fields_ = [("taps", ctypes.c_int), ("kaiser_beta", ctypes.c_double),
-                ("mode", ctypes.c_int), ("n_out", ctypes.c_longlong)]
+                ("mode", ctypes.c_int), ("n_out", ctypes.c_longlong),
+                ("carrier_shift", ctypes.c_int), ("freq_ref", ctypes.c_double)]
 
 
 class DcTuning(ctypes.Structure):
@@ -99,6 +101,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "iono_correct_noalloc": (i, [vp, ll, vp, d, d, d, vp]),
         "correct_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), vp]),
         "correct_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts), vp]),
+        "correct_compress": (i, [vp, vp, ll, vp, ll, vp, d, d, d, d, ctypes.POINTER(DcOpts), vp]),
+        "correct_compress_bank": (i, [vp, vp, ll, vp, ll, dp, i, dp, i, vp, d, d,
+                                      ctypes.POINTER(DcOpts), vp]),
         "resample_exact_batch": (i, [vp, vp, ll, i, ll, dp, i, vp, ll, i, vp]),
         "dc_plan_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), ctypes.POINTER(vp)]),
         "dc_plan_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts),
@@ -132,6 +137,7 @@ def exported_symbols() -> list[str]:
     """Names of the C entry points this binding binds (all declared in dc.h)."""
     return ["dc_opts_default", "dc_status_str", "dc_create", "dc_destroy", "dc_last_error",
             "dc_check", "dc_launch_count", "dc_profile_enable", "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc", "correct_batch", "correct_bank",
+            "correct_compress", "correct_compress_bank",
             "resample_exact_batch", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute",
             "dc_plan_launches", "dc_plan_destroy", "dc_serve_start", "dc_serve_submit",
             "dc_serve_wait", "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop"]
@@ -163,8 +169,10 @@ def _stream(stream) -> int:
     return stream.cuda_stream
 
 
-def _opts(taps=32, beta=8.0, mode=DC_WINDOWED, n_out=0) -> DcOpts:
-    return DcOpts(int(taps), float(beta), int(mode), int(n_out))
+def _opts(taps=32, beta=8.0, mode=DC_WINDOWED, n_out=0, carrier_shift=False,
+          freq_ref=0.0) -> DcOpts:
+    return DcOpts(int(taps), float(beta), int(mode), int(n_out), int(bool(carrier_shift)),
+                  float(freq_ref))
 
 
 def _dptr(a: np.ndarray):
@@ -239,8 +247,9 @@ def dc_profile_read(ctx: Context) -> dict:
 
 
 def doppler_resample(ctx: Context, x, y, fs: float, fc: float, v_r: float, *, taps=32,
-                     beta=8.0, mode=DC_WINDOWED, n_out=0, stream=None) -> None:
-    o = _opts(taps, beta, mode, n_out)
+                     beta=8.0, mode=DC_WINDOWED, n_out=0, carrier_shift=False, freq_ref=0.0,
+                     stream=None) -> None:
+    o = _opts(taps, beta, mode, n_out, carrier_shift, freq_ref)
     ctx.check(ctx.lib.doppler_resample(ctx.handle, _ptr(x), x.numel(), _ptr(y), fs, fc, v_r,
                                        ctypes.byref(o), _stream(stream)))
 
@@ -277,22 +286,45 @@ def iono_correct_noalloc(x, y, fs: float, fc: float, tec_tecu: float, *, stream=
 
 
 def correct_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_WINDOWED,
-                  stream=None) -> None:
+                  carrier_shift=False, freq_ref=0.0, stream=None) -> None:
     """items: numpy array of ITEM_DTYPE (or anything convertible to it)."""
     it = np.ascontiguousarray(np.asarray(items, dtype=ITEM_DTYPE))
-    o = _opts(taps, beta, mode, 0)
+    o = _opts(taps, beta, mode, 0, carrier_shift, freq_ref)
     ctx.check(ctx.lib.correct_batch(ctx.handle, _ptr(inp), _ptr(out), it.ctypes.data, len(it),
                                     ctypes.byref(o), _stream(stream)))
 
 
 def correct_bank(ctx: Context, x, v_r, tec_tecu, out, fs: float, fc: float, *, taps=32,
-                 beta=8.0, n_out=0, stream=None) -> None:
+                 beta=8.0, n_out=0, mode=DC_WINDOWED, carrier_shift=False, freq_ref=0.0,
+                 stream=None) -> None:
     v = np.ascontiguousarray(np.asarray(v_r, dtype=np.float64))
     t = np.ascontiguousarray(np.asarray(tec_tecu, dtype=np.float64))
-    o = _opts(taps, beta, DC_WINDOWED, n_out)
+    o = _opts(taps, beta, mode, n_out, carrier_shift, freq_ref)
     ctx.check(ctx.lib.correct_bank(ctx.handle, _ptr(x), x.numel(), _dptr(v), len(v), _dptr(t),
                                    len(t), _ptr(out, pinned_ok=True), fs, fc, ctypes.byref(o),
                                    _stream(stream)))
+
+
+def correct_compress(ctx: Context, x, replica, y, fs: float, fc: float, v_r: float, tec_tecu: float, *,
+                     taps=32, beta=8.0, mode=DC_WINDOWED, n_out=0, carrier_shift=False, freq_ref=0.0,
+                     stream=None) -> None:
+    """Resample, correct and compress one pulse against `replica` (matched
+    filter in the same frequency-domain pass); y receives the n_out lags."""
+    o = _opts(taps, beta, mode, n_out, carrier_shift, freq_ref)
+    ctx.check(ctx.lib.correct_compress(ctx.handle, _ptr(x), x.numel(), _ptr(replica), replica.numel(),
+                                       _ptr(y), fs, fc, v_r, tec_tecu, ctypes.byref(o), _stream(stream)))
+
+
+def correct_compress_bank(ctx: Context, x, replica, v_r, tec_tecu, out, fs: float, fc: float, *,
+                          taps=32, beta=8.0, n_out=0, mode=DC_WINDOWED, carrier_shift=False,
+                          freq_ref=0.0, stream=None) -> None:
+    v = np.ascontiguousarray(np.asarray(v_r, dtype=np.float64))
+    t = np.ascontiguousarray(np.asarray(tec_tecu, dtype=np.float64))
+    o = _opts(taps, beta, mode, n_out, carrier_shift, freq_ref)
+    ctx.check(ctx.lib.correct_compress_bank(ctx.handle, _ptr(x), x.numel(), _ptr(replica),
+                                            replica.numel(), _dptr(v), len(v), _dptr(t), len(t),
+                                            _ptr(out, pinned_ok=True), fs, fc, ctypes.byref(o),
+                                            _stream(stream)))
 
 
 def resample_exact_batch(ctx: Context, x, n: int, n_pulses: int, v_r, y, *, n_out=0,
@@ -331,9 +363,10 @@ class Plan:
             pass
 
 
-def dc_plan_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_WINDOWED) -> Plan:
+def dc_plan_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_WINDOWED,
+                  carrier_shift=False, freq_ref=0.0) -> Plan:
     it = np.ascontiguousarray(np.asarray(items, dtype=ITEM_DTYPE))
-    o = _opts(taps, beta, mode, 0)
+    o = _opts(taps, beta, mode, 0, carrier_shift, freq_ref)
     h = ctypes.c_void_p()
     ctx.check(ctx.lib.dc_plan_batch(ctx.handle, _ptr(inp), _ptr(out), it.ctypes.data, len(it),
                                     ctypes.byref(o), ctypes.byref(h)))
@@ -341,10 +374,10 @@ def dc_plan_batch(ctx: Context, inp, out, items, *, taps=32, beta=8.0, mode=DC_W
 
 
 def dc_plan_bank(ctx: Context, x, v_r, tec_tecu, out, fs: float, fc: float, *, taps=32, beta=8.0,
-                 n_out=0) -> Plan:
+                 n_out=0, mode=DC_WINDOWED, carrier_shift=False, freq_ref=0.0) -> Plan:
     v = np.ascontiguousarray(np.asarray(v_r, dtype=np.float64))
     t = np.ascontiguousarray(np.asarray(tec_tecu, dtype=np.float64))
-    o = _opts(taps, beta, DC_WINDOWED, n_out)
+    o = _opts(taps, beta, mode, n_out, carrier_shift, freq_ref)
     h = ctypes.c_void_p()
     ctx.check(ctx.lib.dc_plan_bank(ctx.handle, _ptr(x), x.numel(), _dptr(v), len(v), _dptr(t), len(t),
                                    _ptr(out, pinned_ok=True), fs, fc, ctypes.byref(o), ctypes.byref(h)))
@@ -399,9 +432,9 @@ def _host_c64(a, name):
 
 
 def dc_serve_start(device: int = 0, budget_bytes: int = 0, slots: int = 3, *, taps=32, beta=8.0,
-                   mode=DC_WINDOWED) -> Server:
+                   mode=DC_WINDOWED, carrier_shift=False, freq_ref=0.0) -> Server:
     lib = load()
-    o = _opts(taps, beta, mode, 0)
+    o = _opts(taps, beta, mode, 0, carrier_shift, freq_ref)
     h = ctypes.c_void_p()
     st = lib.dc_serve_start(int(device), int(budget_bytes), int(slots), ctypes.byref(o), ctypes.byref(h))
     if st:

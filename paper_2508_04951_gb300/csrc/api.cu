@@ -56,9 +56,10 @@ struct dc_ctx {
   struct Rec { int phase; cudaEvent_t a, b; long long samples; };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> pending;
-  double acc_ms[16] = {};
-  long long acc_launches[16] = {};
-  long long acc_samples[16] = {};
+  static constexpr int kMaxPhases = 24;
+  double acc_ms[kMaxPhases] = {};
+  long long acc_launches[kMaxPhases] = {};
+  long long acc_samples[kMaxPhases] = {};
   // Schedule decisions, 0 = the built-in rule; dc_opts.autotune measures
   // them on a call's own data (see autotune below).
   struct Tune {
@@ -88,11 +89,11 @@ dc_status cuda_fail(dc_ctx* c, cudaError_t e, const char* what) {
 // Kernel phases, named in dc_profile_read().
 enum Ph { PH_RS_TILED, PH_RS_DIRECT, PH_EXACT, PH_ROW_FULL, PH_COL_F1, PH_ROW_MID, PH_COL_B,
           PH_ROW_SPEC, PH_ROW_APPLY, PH_PHASE_TABLE, PH_FUSED_FULL, PH_FUSED_SPEC, PH_FUSED_APPLY,
-          PH_EXACT_TC, PH_COUNT };
+          PH_EXACT_TC, PH_FREQCONV, PH_COUNT };
 const char* kPhaseName[PH_COUNT] = {"resample_tiled", "resample_direct", "exact_fp32", "row_full",
                                     "col_f1", "row_mid", "col_b", "row_spec", "row_apply",
                                     "phase_table", "fused_full", "fused_spec", "fused_apply",
-                                    "exact_tc"};
+                                    "exact_tc", "freqconv"};
 // Transform lengths handled by the cluster-fused kernels.
 bool fused_L(int log2L) { return log2L >= 12 && log2L <= 16; }
 
@@ -151,6 +152,17 @@ struct Phase {
 void split(double v, float& hi, float& lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
+}
+
+// Rotation rate (cycles per output sample) multiplied into a resampled pulse:
+// frequency conversion's tone (freq_ref, plus fc with carrier_shift) or, for
+// the interpolating modes with carrier_shift, the carrier term of a passband
+// dilation, fc (alpha - 1) / fs.  0 when neither applies.
+double rotation_rate(const dc_opts& o, double delta, double fs, double fc) {
+  double f = 0.0;
+  if (o.mode == DC_FREQCONV) f = o.freq_ref + (o.carrier_shift ? fc : 0.0);
+  else if (o.carrier_shift) f = fc;
+  return f * delta / fs;
 }
 
 int log2_ceil(long long n) {
@@ -293,8 +305,11 @@ dc_status check_opts(dc_ctx* c, const dc_opts* o) {
     return fail(c, DC_EINVAL, "taps must be even and in [2, %d], got %d", 2 * kMaxHalf, o->taps);
   if (!(o->kaiser_beta >= 0.0 && o->kaiser_beta <= 20.0))
     return fail(c, DC_EINVAL, "kaiser_beta must be in [0, 20], got %g", o->kaiser_beta);
-  if (o->mode < DC_WINDOWED || o->mode > DC_EXACT_FP16X3)
+  if (o->mode < DC_WINDOWED || o->mode > DC_FREQCONV)
     return fail(c, DC_EINVAL, "unknown mode %d", o->mode);
+  if (o->carrier_shift != 0 && o->carrier_shift != 1)
+    return fail(c, DC_EINVAL, "carrier_shift must be 0 or 1, got %d", o->carrier_shift);
+  if (!std::isfinite(o->freq_ref)) return fail(c, DC_EINVAL, "freq_ref must be finite");
   if (o->n_out < 0 || o->n_out > kMaxN)
     return fail(c, DC_EINVAL, "n_out must be in [0, 2^20], got %lld", o->n_out);
   return DC_OK;
@@ -338,6 +353,27 @@ dc_status upload(dc_ctx* c, const std::vector<T>& v, size_t at, cudaStream_t s, 
 dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, size_t item_at,
                        cudaStream_t s) {
   if (items.empty()) return DC_OK;
+  if (o.mode == DC_FREQCONV) {
+    int tiles = 0;
+    long long outs = 0;
+    for (auto& it : items) {
+      it.tile_begin = tiles;
+      tiles += (int)((it.n_out + kRsTile - 1) / kRsTile);
+      outs += it.n_out;
+    }
+    const RsItem* dev = nullptr;
+    dc_status st = upload(c, items, item_at, s, &dev);
+    if (st) return st;
+    RsArgs a{};
+    a.items = dev;
+    a.n_items = (int)items.size();
+    a.n_tiles = tiles;
+    a.err = c->err;
+    Phase ph(c, PH_FREQCONV, s, outs);
+    cudaError_t e = launch_freqconv(a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "frequency conversion launch");
+    return DC_OK;
+  }
   const std::vector<float> wp = window_poly(o.taps, o.kaiser_beta);
   const float* dwp = nullptr;
   dc_status st = upload(c, wp, item_at, s, &dwp);
@@ -473,6 +509,8 @@ void dc_opts_default(dc_opts* o) {
   o->kaiser_beta = 8.0;
   o->mode = DC_WINDOWED;
   o->n_out = 0;
+  o->carrier_shift = 0;
+  o->freq_ref = 0.0;
 }
 
 const char* dc_status_str(int s) {
@@ -555,7 +593,8 @@ dc_status dc_profile_enable(dc_ctx* c, int on) {
     c->pool.push_back(r.b);
   }
   c->pending.clear();
-  for (int i = 0; i < 16; ++i) c->acc_ms[i] = 0, c->acc_launches[i] = 0, c->acc_samples[i] = 0;
+  for (int i = 0; i < dc_ctx::kMaxPhases; ++i)
+    c->acc_ms[i] = 0, c->acc_launches[i] = 0, c->acc_samples[i] = 0;
   c->profiling = on != 0;
   return DC_OK;
 }
@@ -632,20 +671,24 @@ dc_status doppler_resample(dc_ctx* c, const dc_c64* x, long long n, dc_c64* y, d
   const double dl = alpha_minus_one(v_r);
   cudaStream_t s = S(stream);
   if ((st = ensure_items(c, items_bytes_for(4)))) return st;
-  if (o.mode == DC_WINDOWED) {
+  if (o.mode == DC_WINDOWED || o.mode == DC_FREQCONV) {
     std::vector<RsItem> items(1);
+    items[0] = RsItem{};
     items[0].x = reinterpret_cast<const float2*>(x);
     items[0].y = reinterpret_cast<float2*>(y);
     items[0].n_in = (int)n;
     items[0].n_out = (int)n_out;
     split(dl, items[0].dl_hi, items[0].dl_lo);
+    split(rotation_rate(o, dl, fs, fc), items[0].rot_hi, items[0].rot_lo);
     return run_windowed(c, items, o, 0, s);
   }
   if (o.mode != DC_EXACT_FP32) return fail(c, DC_EINVAL, "single-pulse exact resampling uses FP32");
   std::vector<ExItem> ex(1);
+  ex[0] = ExItem{};
   ex[0].x = reinterpret_cast<const float2*>(x);
   ex[0].y = reinterpret_cast<float2*>(y);
   split(dl, ex[0].dl_hi, ex[0].dl_lo);
+  split(rotation_rate(o, dl, fs, fc), ex[0].rot_hi, ex[0].rot_lo);
   const ExItem* dev = nullptr;
   if ((st = upload(c, ex, 0, s, &dev))) return st;
   ExArgs a{dev, (int)n, (int)n_out, 1};
@@ -690,8 +733,8 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
   if (n_items < 0 || (n_items > 0 && (!items || !in || !out)))
     return fail(c, DC_EINVAL, "bad item list");
   if (n_items == 0) return DC_OK;
-  if (o.mode != DC_WINDOWED && o.mode != DC_EXACT_FP32)
-    return fail(c, DC_EINVAL, "correct_batch supports DC_WINDOWED and DC_EXACT_FP32");
+  if (o.mode != DC_WINDOWED && o.mode != DC_EXACT_FP32 && o.mode != DC_FREQCONV)
+    return fail(c, DC_EINVAL, "correct_batch supports DC_WINDOWED, DC_EXACT_FP32 and DC_FREQCONV");
   for (int i = 0; i < n_items; ++i) {
     const dc_item& it = items[i];
     const long long no = it.n_out ? it.n_out : it.n;
@@ -728,15 +771,18 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
   size_t item_at = 0;
 
   // 1. resampling
-  if (o.mode == DC_WINDOWED) {
+  if (o.mode == DC_WINDOWED || o.mode == DC_FREQCONV) {
     std::vector<RsItem> rs(n_items);
     for (int i = 0; i < n_items; ++i) {
       const dc_item& it = items[i];
+      const double dl = alpha_minus_one(it.v_r);
+      rs[i] = RsItem{};
       rs[i].x = X + it.in_off;
       rs[i].y = reinterpret_cast<float2*>(ws + yoff[i]);
       rs[i].n_in = (int)it.n;
       rs[i].n_out = (int)(it.n_out ? it.n_out : it.n);
-      split(alpha_minus_one(it.v_r), rs[i].dl_hi, rs[i].dl_lo);
+      split(dl, rs[i].dl_hi, rs[i].dl_lo);
+      split(rotation_rate(o, dl, it.fs, it.fc), rs[i].rot_hi, rs[i].rot_lo);
     }
     if ((st = run_windowed(c, rs, o, item_at, s))) return st;
     item_at += 2 * ((n_items * sizeof(RsItem) + 255) & ~(size_t)255) + 4096;
@@ -744,9 +790,12 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
     for (int i = 0; i < n_items; ++i) {
       const dc_item& it = items[i];
       std::vector<ExItem> ex(1);
+      const double dl = alpha_minus_one(it.v_r);
+      ex[0] = ExItem{};
       ex[0].x = X + it.in_off;
       ex[0].y = reinterpret_cast<float2*>(ws + yoff[i]);
-      split(alpha_minus_one(it.v_r), ex[0].dl_hi, ex[0].dl_lo);
+      split(dl, ex[0].dl_hi, ex[0].dl_lo);
+      split(rotation_rate(o, dl, it.fs, it.fc), ex[0].rot_hi, ex[0].rot_lo);
       const ExItem* dev = nullptr;
       if ((st = upload(c, ex, item_at, s, &dev))) return st;
       item_at += 256;
@@ -793,27 +842,91 @@ __global__ void stuck_wait_kernel(int* err, int polls) {
   atomicExch(err, 1);
 }
 
-// fused != 0: the layout of the cluster-fused kernels -- element k1*4096 + k2
-// holds bin k1 + L1 k2 (L1 = L/4096) -- with the inverse transform's 1/L folded in.
-__global__ void phase_table_kernel(const PhaseParams* ph, int n_tec, int log2L, int fused,
-                                   float2* P) {
+// Factor tables P[t][.] in the spectrum layout (element k1*4096 + k2 holds
+// bin k1 + L1 k2, L1 = L/4096, for L > 4096; natural order for L <= 4096 --
+// the same formula with L1 = 1): exp(-i phi_k(TEC_t)) times `scale` (1/L
+// for the spectrum-apply kernel, which folds in the inverse transform's
+// factor; else 1).  H (optional): a replica's spectrum in the same layout;
+// each factor is then multiplied by conj(H_k), the matched filter of pulse
+// compression (Sec. II-B).
+__global__ void phase_table_kernel(const PhaseParams* ph, int n_tec, int log2L, float scale,
+                                   const float2* H, float2* P) {
   const size_t L = (size_t)1 << log2L;
   const size_t total = L * (size_t)n_tec;
   const int log2L1 = log2L > 12 ? log2L - 12 : 0;
-  const float scale = fused ? 1.0f / (float)L : 1.0f;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total;
        g += (size_t)gridDim.x * blockDim.x) {
     const int t = (int)(g >> log2L), idx = (int)(g & (L - 1));
-    const int k = fused ? ((idx >> 12) + ((idx & 4095) << log2L1)) : idx;
-    const float2 w = ph[t].enabled ? iono_factor(ph[t], k) : make_float2(1.f, 0.f);
+    const int k = (idx >> 12) + ((idx & 4095) << log2L1);
+    float2 w = ph[t].enabled ? iono_factor(ph[t], k) : make_float2(1.f, 0.f);
+    if (H) {
+      const float2 h = __ldg(H + idx);
+      w = cmul(w, make_float2(h.x, -h.y));
+    }
     P[g] = cscale(w, scale);
   }
 }
 }  // namespace dc
 
-extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const double* v_r,
-                                  int n_v, const double* tec, int n_tec, dc_c64* out, double fs,
-                                  double fc, const dc_opts* opts, void* stream) {
+namespace {
+
+// Forward spectra of the items' sources (zero-padded past n_valid) into their
+// dst, length L = 2^log2L, in the spectrum layout (bin k1 + L1 k2 at
+// k1*4096 + k2 for L > 4096, natural order below): cluster-fused, one row
+// pass, or the first two passes of the four-step split (T: L samples per
+// item of scratch).
+dc_status run_spectra(dc_ctx* c, std::vector<FftItem>& sp, int log2L, float2* T, size_t& item_at,
+                      cudaStream_t s) {
+  const int n_sp = (int)sp.size();
+  const bool four = log2L > 12;
+  const size_t L = (size_t)1 << log2L;
+  long long samples = 0;
+  for (auto& f : sp) samples += f.n_valid;
+  const FftItem* dev = nullptr;
+  dc_status st;
+  cudaError_t e;
+  if (use_fused(c, log2L)) {
+    if ((st = upload(c, sp, item_at, s, &dev))) return st;
+    item_at += (n_sp * sizeof(FftItem) + 255) & ~(size_t)255;
+    FusedArgs a{dev, n_sp, log2L, c->tw, c->err, c->t4};
+    Phase ph(c, PH_FUSED_SPEC, s, samples);
+    if ((e = launch_fused(FUSED_SPEC, a, s)) != cudaSuccess) return cuda_fail(c, e, "spec launch");
+  } else if (!four) {
+    if ((st = upload(c, sp, item_at, s, &dev))) return st;
+    item_at += (n_sp * sizeof(FftItem) + 255) & ~(size_t)255;
+    RowArgs a{dev, n_sp, log2L, 0, c->tw};
+    Phase ph(c, PH_ROW_SPEC, s, samples);
+    if ((e = launch_row(ROW_SPEC, a, s)) != cudaSuccess) return cuda_fail(c, e, "spec launch");
+  } else {
+    std::vector<FftItem> f1 = sp, f2 = sp;
+    for (int i = 0; i < n_sp; ++i) {
+      f1[i].dst = T + (size_t)i * L;
+      f2[i].src = T + (size_t)i * L;
+    }
+    if ((st = upload(c, f1, item_at, s, &dev))) return st;
+    item_at += (n_sp * sizeof(FftItem) + 255) & ~(size_t)255;
+    ColArgs a1{dev, n_sp, log2L, log2L - 12, c->tw};
+    {
+      Phase ph(c, PH_COL_F1, s, samples);
+      if ((e = launch_col(COL_F1, a1, s)) != cudaSuccess) return cuda_fail(c, e, "F1 launch");
+    }
+    if ((st = upload(c, f2, item_at, s, &dev))) return st;
+    item_at += (n_sp * sizeof(FftItem) + 255) & ~(size_t)255;
+    RowArgs a2{dev, n_sp, log2L, log2L - 12, c->tw};
+    Phase ph(c, PH_ROW_SPEC, s, samples);
+    if ((e = launch_row(ROW_SPEC, a2, s)) != cudaSuccess) return cuda_fail(c, e, "F2 launch");
+  }
+  return DC_OK;
+}
+
+// The Doppler bank (correct_bank), and with a replica (rep, n_rep samples)
+// the bank compressed against it (correct_compress_bank): the replica's
+// spectrum is computed with the range rates' spectra and its conjugate
+// folded into every TEC's factor table, so the phase-and-inverse pass is
+// unchanged (Sec. II-B's bundling of the correction with pulse compression).
+dc_status bank_impl(dc_ctx* c, const dc_c64* x, long long n, const dc_c64* rep, long long n_rep,
+                    const double* v_r, int n_v, const double* tec, int n_tec, dc_c64* out,
+                    double fs, double fc, const dc_opts* opts, void* stream) {
   if (!c) return DC_EINVAL;
   std::lock_guard<std::recursive_mutex> g(c->mu);
   dc_opts o;
@@ -821,7 +934,8 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   if (opts) o = *opts;
   dc_status st = check_opts(c, &o);
   if (st) return st;
-  if (o.mode != DC_WINDOWED) return fail(c, DC_EINVAL, "correct_bank supports DC_WINDOWED");
+  if (o.mode != DC_WINDOWED && o.mode != DC_FREQCONV)
+    return fail(c, DC_EINVAL, "the bank supports DC_WINDOWED and DC_FREQCONV");
   if (n_v < 1 || n_tec < 1 || !v_r || !tec || !x || !out)
     return fail(c, DC_EINVAL, "bad bank lists");
   const long long n_out = o.n_out ? o.n_out : n;
@@ -829,25 +943,29 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     if ((st = check_pulse(c, n, n_out, fs, fc, v_r[i], 0.0))) return st;
   for (int t = 0; t < n_tec; ++t)
     if (!std::isfinite(tec[t])) return fail(c, DC_EINVAL, "tec[%d] not finite", t);
-  cudaSetDevice(c->device);
-  cudaStream_t s = S(stream);
   const int log2L = log2_ceil(n_out);
   const size_t L = (size_t)1 << log2L;
+  const bool compress = rep != nullptr;
+  if (compress && (n_rep < 1 || (size_t)n_rep > L))
+    return fail(c, DC_EINVAL, "replica length %lld outside [1, L = %zu]", n_rep, L);
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
   const bool four = log2L > 12;
   const bool fused = use_fused(c, log2L);
   // Transforms per chunk of the inverse (four-step T kept small enough to
   // stay in L2 between its two passes).
   const int chunk =
       four ? (int)chunk_items(c, log2L, (size_t)n_v * n_tec, (size_t)64 << 20) : n_v * n_tec;
+  const int n_sp = n_v + (compress ? 1 : 0);     // spectra: one per v_r, then the replica's
   Arena ar;
   const size_t y_at = ar.take((size_t)n_v * n_out * sizeof(float2));
   const size_t p_at = ar.take((size_t)n_tec * L * sizeof(float2));
-  const size_t s_at = ar.take((size_t)n_v * L * sizeof(float2));
+  const size_t s_at = ar.take((size_t)n_sp * L * sizeof(float2));
   const size_t t_at =
-      ar.take(fused ? 0 : (size_t)std::max(chunk, four ? n_v : 0) * L * sizeof(float2));
+      ar.take(fused ? 0 : (size_t)std::max(chunk, four ? n_sp : 0) * L * sizeof(float2));
   if ((st = ensure_ws(c, ar.off))) return st;
   const size_t n_pairs = (size_t)n_v * n_tec;
-  if ((st = ensure_items(c, items_bytes_for(n_pairs * 2 + n_v * 6 + n_tec)))) return st;
+  if ((st = ensure_items(c, items_bytes_for(n_pairs * 2 + n_sp * 6 + n_tec)))) return st;
   char* ws = c->ws;
   float2* Yr = reinterpret_cast<float2*>(ws + y_at);
   float2* P = reinterpret_cast<float2*>(ws + p_at);
@@ -856,7 +974,34 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   size_t item_at = 0;
   cudaError_t e;
 
-  // 1. phase table
+  // 1. resample per v_r
+  std::vector<RsItem> rs(n_v);
+  for (int i = 0; i < n_v; ++i) {
+    const double dl = alpha_minus_one(v_r[i]);
+    rs[i] = RsItem{};
+    rs[i].x = reinterpret_cast<const float2*>(x);
+    rs[i].y = Yr + (size_t)i * n_out;
+    rs[i].n_in = (int)n;
+    rs[i].n_out = (int)n_out;
+    split(dl, rs[i].dl_hi, rs[i].dl_lo);
+    split(rotation_rate(o, dl, fs, fc), rs[i].rot_hi, rs[i].rot_lo);
+  }
+  if ((st = run_windowed(c, rs, o, item_at, s))) return st;
+  item_at += 2 * ((n_v * sizeof(RsItem) + 255) & ~(size_t)255) + 4096;
+  // 2. spectra per v_r (and of the zero-padded replica): four-step layout
+  // for L > 4096, natural order below
+  std::vector<FftItem> sp(n_sp);
+  for (int i = 0; i < n_sp; ++i) {
+    const bool is_rep = i == n_v;
+    sp[i] = FftItem{};
+    sp[i].src = is_rep ? reinterpret_cast<const float2*>(rep) : Yr + (size_t)i * n_out;
+    sp[i].dst = Sp + (size_t)i * L;
+    sp[i].n_valid = (int)(is_rep ? n_rep : n_out);
+    sp[i].n_out = sp[i].n_valid;
+  }
+  if ((st = run_spectra(c, sp, log2L, T, item_at, s))) return st;
+  // 3. factor table per TEC: exp(-i phi_k) (times conj of the replica's
+  // spectrum when compressing), in the layout the inverse pass reads
   std::vector<PhaseParams> ph(n_tec);
   for (int t = 0; t < n_tec; ++t) ph[t] = phase_params(fs, fc, tec[t], log2L);
   const PhaseParams* dph = nullptr;
@@ -866,62 +1011,12 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
     const size_t total = L * n_tec;
     const int grid = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
     Phase phs(c, PH_PHASE_TABLE, s, (long long)total);
-    phase_table_kernel<<<grid, 256, 0, s>>>(dph, n_tec, log2L, fused ? 1 : 0, P);
+    phase_table_kernel<<<grid, 256, 0, s>>>(dph, n_tec, log2L, fused ? 1.0f / (float)L : 1.0f,
+                                            compress ? Sp + (size_t)n_v * L : nullptr, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "phase table launch");
   }
-  // 2. resample per v_r
-  std::vector<RsItem> rs(n_v);
-  for (int i = 0; i < n_v; ++i) {
-    rs[i].x = reinterpret_cast<const float2*>(x);
-    rs[i].y = Yr + (size_t)i * n_out;
-    rs[i].n_in = (int)n;
-    rs[i].n_out = (int)n_out;
-    split(alpha_minus_one(v_r[i]), rs[i].dl_hi, rs[i].dl_lo);
-  }
-  if ((st = run_windowed(c, rs, o, item_at, s))) return st;
-  item_at += 2 * ((n_v * sizeof(RsItem) + 255) & ~(size_t)255) + 4096;
-  // 3. spectra per v_r
-  std::vector<FftItem> sp(n_v);
-  for (int i = 0; i < n_v; ++i) {
-    sp[i] = FftItem{};
-    sp[i].src = Yr + (size_t)i * n_out;
-    sp[i].dst = Sp + (size_t)i * L;
-    sp[i].n_valid = (int)n_out;
-    sp[i].n_out = (int)n_out;
-  }
+  // 4. factors + inverse per (v_r, TEC), in chunks
   const FftItem* dev = nullptr;
-  if (fused) {
-    if ((st = upload(c, sp, item_at, s, &dev))) return st;
-    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
-    FusedArgs a{dev, n_v, log2L, c->tw, c->err, c->t4};
-    Phase ph(c, PH_FUSED_SPEC, s, (long long)n_v * n_out);
-    if ((e = launch_fused(FUSED_SPEC, a, s)) != cudaSuccess) return cuda_fail(c, e, "spec launch");
-  } else if (!four) {
-    if ((st = upload(c, sp, item_at, s, &dev))) return st;
-    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
-    RowArgs a{dev, n_v, log2L, 0, c->tw};
-    Phase ph(c, PH_ROW_SPEC, s, (long long)n_v * n_out);
-    if ((e = launch_row(ROW_SPEC, a, s)) != cudaSuccess) return cuda_fail(c, e, "spec launch");
-  } else {
-    std::vector<FftItem> f1 = sp, f2 = sp;
-    for (int i = 0; i < n_v; ++i) {
-      f1[i].dst = T + (size_t)i * L;
-      f2[i].src = T + (size_t)i * L;
-    }
-    if ((st = upload(c, f1, item_at, s, &dev))) return st;
-    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
-    ColArgs a1{dev, n_v, log2L, log2L - 12, c->tw};
-    {
-      Phase ph(c, PH_COL_F1, s, (long long)n_v * n_out);
-      if ((e = launch_col(COL_F1, a1, s)) != cudaSuccess) return cuda_fail(c, e, "F1 launch");
-    }
-    if ((st = upload(c, f2, item_at, s, &dev))) return st;
-    item_at += (n_v * sizeof(FftItem) + 255) & ~(size_t)255;
-    RowArgs a2{dev, n_v, log2L, log2L - 12, c->tw};
-    Phase ph(c, PH_ROW_SPEC, s, (long long)n_v * n_out);
-    if ((e = launch_row(ROW_SPEC, a2, s)) != cudaSuccess) return cuda_fail(c, e, "F2 launch");
-  }
-  // 4. phase + inverse per (v_r, TEC), in chunks
   std::vector<FftItem> ap(n_pairs);
   for (int i = 0; i < n_v; ++i)
     for (int t = 0; t < n_tec; ++t) {
@@ -973,6 +1068,118 @@ extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const
   return DC_OK;
 }
 
+}  // namespace
+
+extern "C" dc_status correct_bank(dc_ctx* c, const dc_c64* x, long long n, const double* v_r,
+                                  int n_v, const double* tec, int n_tec, dc_c64* out, double fs,
+                                  double fc, const dc_opts* opts, void* stream) {
+  return bank_impl(c, x, n, nullptr, 0, v_r, n_v, tec, n_tec, out, fs, fc, opts, stream);
+}
+
+extern "C" dc_status correct_compress_bank(dc_ctx* c, const dc_c64* x, long long n,
+                                           const dc_c64* replica, long long n_rep,
+                                           const double* v_r, int n_v, const double* tec,
+                                           int n_tec, dc_c64* out, double fs, double fc,
+                                           const dc_opts* opts, void* stream) {
+  if (!replica) return fail(c, DC_EINVAL, "null replica");
+  return bank_impl(c, x, n, replica, n_rep, v_r, n_v, tec, n_tec, out, fs, fc, opts, stream);
+}
+
+extern "C" dc_status correct_compress(dc_ctx* c, const dc_c64* x, long long n,
+                                      const dc_c64* replica, long long n_rep, dc_c64* y, double fs,
+                                      double fc, double v_r, double tec, const dc_opts* opts,
+                                      void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  dc_opts o;
+  dc_opts_default(&o);
+  if (opts) o = *opts;
+  dc_status st = check_opts(c, &o);
+  if (st) return st;
+  if (o.mode != DC_WINDOWED && o.mode != DC_EXACT_FP32 && o.mode != DC_FREQCONV)
+    return fail(c, DC_EINVAL, "correct_compress supports DC_WINDOWED, DC_EXACT_FP32 and DC_FREQCONV");
+  const long long n_out = o.n_out ? o.n_out : n;
+  if ((st = check_pulse(c, n, n_out, fs, fc, v_r, tec))) return st;
+  if (!x || !y || !replica) return fail(c, DC_EINVAL, "null buffer");
+  const int log2L = log2_ceil(n_out);
+  const size_t L = (size_t)1 << log2L;
+  if (n_rep < 1 || (size_t)n_rep > L)
+    return fail(c, DC_EINVAL, "replica length %lld outside [1, L = %zu]", n_rep, L);
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
+  // scratch: resampled pulse, replica spectrum, factor table, four-step T
+  Arena ar;
+  const size_t y_at = ar.take((size_t)n_out * sizeof(float2));
+  const size_t h_at = ar.take(L * sizeof(float2));
+  const size_t p_at = ar.take(L * sizeof(float2));
+  const size_t t_at = ar.take(log2L > 12 ? L * sizeof(float2) : 0);
+  if ((st = ensure_ws(c, ar.off))) return st;
+  if ((st = ensure_items(c, items_bytes_for(16)))) return st;
+  char* ws = c->ws;
+  float2* Yr = reinterpret_cast<float2*>(ws + y_at);
+  float2* H = reinterpret_cast<float2*>(ws + h_at);
+  float2* P = reinterpret_cast<float2*>(ws + p_at);
+  float2* T = reinterpret_cast<float2*>(ws + t_at);
+  size_t item_at = 0;
+  cudaError_t e;
+  const double dl = alpha_minus_one(v_r);
+  // 1. resampling
+  if (o.mode == DC_EXACT_FP32) {
+    std::vector<ExItem> ex(1);
+    ex[0] = ExItem{};
+    ex[0].x = reinterpret_cast<const float2*>(x);
+    ex[0].y = Yr;
+    split(dl, ex[0].dl_hi, ex[0].dl_lo);
+    split(rotation_rate(o, dl, fs, fc), ex[0].rot_hi, ex[0].rot_lo);
+    const ExItem* dev = nullptr;
+    if ((st = upload(c, ex, item_at, s, &dev))) return st;
+    item_at += 256;
+    ExArgs a{dev, (int)n, (int)n_out, 1};
+    Phase ph(c, PH_EXACT, s, n_out);
+    if ((e = launch_exact_fp32(a, 1, s)) != cudaSuccess) return cuda_fail(c, e, "exact launch");
+  } else {
+    std::vector<RsItem> rs(1);
+    rs[0] = RsItem{};
+    rs[0].x = reinterpret_cast<const float2*>(x);
+    rs[0].y = Yr;
+    rs[0].n_in = (int)n;
+    rs[0].n_out = (int)n_out;
+    split(dl, rs[0].dl_hi, rs[0].dl_lo);
+    split(rotation_rate(o, dl, fs, fc), rs[0].rot_hi, rs[0].rot_lo);
+    if ((st = run_windowed(c, rs, o, item_at, s))) return st;
+    item_at += 2 * 256 + 4096;
+  }
+  // 2. the replica's spectrum (zero-padded to L)
+  std::vector<FftItem> sp(1);
+  sp[0] = FftItem{};
+  sp[0].src = reinterpret_cast<const float2*>(replica);
+  sp[0].dst = H;
+  sp[0].n_valid = (int)n_rep;
+  sp[0].n_out = (int)n_rep;
+  if ((st = run_spectra(c, sp, log2L, T, item_at, s))) return st;
+  // 3. factors exp(-i phi_k) conj(H_k) in the spectrum layout
+  std::vector<PhaseParams> ph(1, phase_params(fs, fc, tec, log2L));
+  const PhaseParams* dph = nullptr;
+  if ((st = upload(c, ph, item_at, s, &dph))) return st;
+  item_at += 256;
+  {
+    const int grid = (int)std::min<size_t>((L + 255) / 256, 152 * 16);
+    Phase phs(c, PH_PHASE_TABLE, s, (long long)L);
+    phase_table_kernel<<<grid, 256, 0, s>>>(dph, 1, log2L, 1.0f, H, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "factor table launch");
+  }
+  // 4. forward transform, factors, inverse transform, first n_out lags
+  std::vector<FftItem> it(1);
+  it[0] = FftItem{};
+  it[0].src = Yr;
+  it[0].dst = reinterpret_cast<float2*>(y);
+  it[0].ptab = P;
+  it[0].ph = ph[0];
+  it[0].n_valid = (int)n_out;
+  it[0].n_out = (int)n_out;
+  return run_iono_class(c, it, log2L, T, 1, item_at, s);
+}
+
 extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long n, int n_pulses,
                                           long long stride, const double* v_r, int n_alpha,
                                           dc_c64* y, long long n_out, int mode, void* stream) {
@@ -1015,6 +1222,7 @@ extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long 
   if ((st = ensure_items(c, items_bytes_for(n_alpha)))) return st;
   std::vector<ExItem> ex(n_alpha);
   for (int i = 0; i < n_alpha; ++i) {
+    ex[i] = ExItem{};
     ex[i].x = reinterpret_cast<const float2*>(x) + (size_t)i * stride;
     ex[i].y = reinterpret_cast<float2*>(y) + (size_t)i * n_pulses * n_out;
     split(alpha_minus_one(v_r[i]), ex[i].dl_hi, ex[i].dl_lo);
@@ -1317,7 +1525,7 @@ extern "C" dc_status dc_autotune_bank(dc_ctx* c, const dc_c64* x, long long n, c
   bool q8 = false;
   for (int i = 0; i < n_v; ++i)
     if (std::fabs(v_r[i]) < kC) q8 |= resample_q(std::fabs(alpha_minus_one(v_r[i]))) == 8;
-  if (o.taps == 32 && q8) ch.push_back({0, 0, {8, 4}});
+  if (o.mode == DC_WINDOWED && o.taps == 32 && q8) ch.push_back({0, 0, {8, 4}});
   class_choices(ch, log2_ceil(n_out), (size_t)n_v * n_tec);
   cudaSetDevice(c->device);
   cudaStream_t s = S(stream);

@@ -73,6 +73,21 @@ DC_DEV df df_div(df a, df b) {
   return two_sum(q1, q2);
 }
 
+// exp(2 pi i g n) for a rotation rate g (cycles per sample) held as the
+// double-float g_hi + g_lo and an output index n < 2^24: g n is formed as a
+// double-float (two_prod, exact for the high part), its integer part removed
+// exactly (rintf of the high part), and the remaining fraction of a cycle
+// goes to sincospif.  Used for the carrier term of a passband dilation and
+// for frequency conversion, whose phases reach thousands of cycles.
+DC_DEV float2 cycles_rot(float g_hi, float g_lo, int n) {
+  const float fn = (float)n;
+  const df p = two_prod(g_hi, fn);
+  const float r = __fadd_rn(__fsub_rn(p.hi, rintf(p.hi)), fmaf(g_lo, fn, p.lo));
+  float s, c;
+  sincospif(2.0f * r, &s, &c);
+  return make_float2(c, s);
+}
+
 // --------------------------------------------------------- radix-R DFTs
 // DIR = -1: forward, exp(-2 pi i kn/R); DIR = +1: inverse (no 1/R).
 // Output in natural order, in place.

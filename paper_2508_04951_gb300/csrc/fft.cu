@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kThreads) row_kernel(RowArgs a) {
       }
       if (OP == ROW_APPLY) {
         const int k = row + L1 * p;
-        if (I.ptab) v = cmul(v, __ldg(I.ptab + k));
+        // the table is in the spectrum's own layout: bin k at row * M + p
+        if (I.ptab) v = cmul(v, __ldg(I.ptab + (size_t)row * M + p));
         else if (I.ph.enabled) v = cmul(v, iono_factor(I.ph, k));
       }
     }
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) row_kernel(RowArgs a) {
         const FftItem& I = a.items[it];
         const int k = row + L1 * p;
         float2 w;
-        if (I.ptab) w = __ldg(I.ptab + k);
+        if (I.ptab) w = __ldg(I.ptab + (size_t)row * M + p);   // the spectrum's layout
         else if (I.ph.enabled) w = iono_factor(I.ph, k);
         else continue;
         sm[c * LP + rpad(p)] = cmul(sm[c * LP + rpad(p)], w);

@@ -24,8 +24,12 @@ namespace dc {
 struct FftItem {
   const float2* src;     // input of this pass
   float2* dst;           // output of this pass
-  const float2* ptab;    // correction factors exp(-i phi_k), natural bin order
-                         // (length L); null -> computed from `ph`
+  const float2* ptab;    // per-bin factors (length L): exp(-i phi_k), times a
+                         // matched filter's conjugate replica spectrum when
+                         // compressing, in the spectrum's layout (bin
+                         // k1 + L1 k2 at k1*4096 + k2 for L > 4096, natural
+                         // order below); null -> exp(-i phi_k) computed from
+                         // `ph`
   PhaseParams ph;
   int n_valid;           // samples of src that are data (zero beyond), first pass
   int n_out;             // samples stored by the last pass (truncation)

@@ -135,6 +135,25 @@ DC_DEV void row4096_1buf_arrive(float2 (&v)[16], float2* b, int j, const float2*
   dft16<DIR>(v);
 }
 
+// The per-bin factors of the full correction on 16 bins k0 + s i held by one
+// thread: the caller's table (I.ptab, in the four-step layout, entries
+// t0 .. t0 + 15: exp(-i phi_k) times anything else the call bundles into the
+// frequency domain, e.g. a matched filter's conjugate replica spectrum) when
+// there is one, else exp(-i phi_k) of Eq. 16 from the phase constants.
+DC_DEV void bin_factors(const FftItem& I, int k0, int s, int t0, float2 (&u)[16]) {
+  if (I.ptab) {
+    const float4* t = reinterpret_cast<const float4*>(I.ptab + t0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 w = __ldg(t + i);
+      u[2 * i] = cmul(u[2 * i], make_float2(w.x, w.y));
+      u[2 * i + 1] = cmul(u[2 * i + 1], make_float2(w.z, w.w));
+    }
+  } else {
+    iono_apply_run16(I.ph, k0, s, u);
+  }
+}
+
 // Wait half of a split cluster barrier (acquire), after an arrive.release.
 template <int CL> DC_DEV void cluster_wait() {
   if constexpr (CL > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -382,7 +401,8 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
       v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
     }
     row4096<-1>(v, A, B, j, f2, f3);            // last reads: B after its second barrier
-    if (I.ph.enabled) {
+    const bool mult = I.ph.enabled || I.ptab;
+    if (mult) {
       // regroup through A (last read before the forward's second barrier)
 #pragma unroll
       for (int r = 0; r < 16; ++r) A[pad16(j + 256 * r)] = v[r];
@@ -390,7 +410,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
       float2 u[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
-      iono_apply_run16(I.ph, 16 * j, 1, u);
+      bin_factors(I, 16 * j, 1, 16 * j, u);
 #pragma unroll
       for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
       __syncthreads();
@@ -401,7 +421,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
     // the inverse row writes first the buffer no thread can still be reading
-    if (I.ph.enabled) row4096<+1>(v, B, A, j, f2, f3);
+    if (mult) row4096<+1>(v, B, A, j, f2, f3);
     else row4096<+1>(v, A, B, j, f2, f3);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -441,7 +461,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
     for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
     __syncthreads();                            // the row FFT overwrites A
     row4096_1buf<-1>(v, A, j, a.tw);
-    if (I.ph.enabled) {
+    if (I.ph.enabled || I.ptab) {
       // the forward row's last stage read A at exactly the addresses this
       // thread writes first, so no barrier is needed before the regroup
 #pragma unroll
@@ -450,7 +470,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
       float2 u[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
-      iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
+      bin_factors(I, k1 + L1 * 16 * j, L1, k1 * kRowN + 16 * j, u);
 #pragma unroll
       for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
       __syncthreads();
@@ -540,8 +560,8 @@ __global__ void __launch_bounds__(kRowThreads, 4) row_mid_kernel(RowArgs a) {
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = src[j + 256 * r];
   row4096_1buf<-1>(v, bufA, j, a.tw);
-  if (I.ph.enabled) {
-    // phase of bin k = k1 + L1 k2, each thread on 16 consecutive k2 (the
+  if (I.ph.enabled || I.ptab) {
+    // factor of bin k = k1 + L1 k2, each thread on 16 consecutive k2 (the
     // forward row's last stage read A at exactly the addresses this thread
     // writes now, so no barrier is needed first)
 #pragma unroll
@@ -550,7 +570,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) row_mid_kernel(RowArgs a) {
     float2 u[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) u[i] = bufA[pad16(16 * j + i)];
-    iono_apply_run16(I.ph, k1 + L1 * 16 * j, L1, u);
+    bin_factors(I, k1 + L1 * 16 * j, L1, k1 * kRowN + 16 * j, u);
 #pragma unroll
     for (int i = 0; i < 16; ++i) bufA[pad16(16 * j + i)] = u[i];
     __syncthreads();

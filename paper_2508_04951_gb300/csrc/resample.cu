@@ -64,6 +64,12 @@ DC_DEV float tap_weight(const RsArgs& a, float e, float s_e, int k) {
   return sc * window_at(a.wpoly, k + a.half - 1, e);
 }
 
+// v exp(2 pi i g n) (the item's carrier rotation), or v when g = 0.
+DC_DEV float2 rotate(float2 v, float g_hi, float g_lo, int n) {
+  if (g_hi == 0.f && g_lo == 0.f) return v;
+  return cmul(v, cycles_rot(g_hi, g_lo, n));
+}
+
 // The item owning a tile: the last item with tile_begin <= tile (tile_begin
 // strictly increases).  One warp probes 32 evenly spaced items per round, so
 // the search takes ceil(log32 n_items) dependent loads instead of log2.
@@ -114,7 +120,27 @@ __global__ void __launch_bounds__(kRsThreads) resample_direct_kernel(RsArgs a) {
         acc.y = fmaf(v.y, h, acc.y);
       }
     }
-    I.y[i] = acc;
+    I.y[i] = rotate(acc, I.rot_hi, I.rot_lo, i);
+  }
+}
+
+// ---------------------------------------------------- frequency conversion
+__global__ void __launch_bounds__(kRsThreads) freqconv_kernel(RsArgs a) {
+  __shared__ int s_item;
+  const int tile = blockIdx.x;
+  if (threadIdx.x < 32) {
+    const int it = find_item(a, tile);
+    if (threadIdx.x == 0) s_item = it;
+  }
+  __syncthreads();
+  const RsItem& I = a.items[s_item];
+  const int o0 = (tile - I.tile_begin) * kRsTile;
+#pragma unroll
+  for (int q = 0; q < kRsTile / kRsThreads; ++q) {
+    const int i = o0 + q * kRsThreads + threadIdx.x;
+    if (i >= I.n_out) break;
+    const float2 v = i < I.n_in ? __ldg(I.x + i) : make_float2(0.f, 0.f);
+    __stcs(I.y + i, rotate(v, I.rot_hi, I.rot_lo, i));
   }
 }
 
@@ -340,19 +366,28 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   __syncwarp();
   const int n_here = min(W, I.n_out - ow);
   float2* y = I.y + ow;
+  const bool rot = I.rot_hi != 0.f || I.rot_lo != 0.f;    // carrier term
   if ((reinterpret_cast<uintptr_t>(y) & 15) == 0) {
-    for (int p = lane; 2 * p + 1 < n_here; p += 32)
-      __stcs(reinterpret_cast<float4*>(y) + p, s4[p ^ ((p >> 3) & 7)]);
+    for (int p = lane; 2 * p + 1 < n_here; p += 32) {
+      float4 t = s4[p ^ ((p >> 3) & 7)];
+      if (rot) {
+        const float2 u = rotate(make_float2(t.x, t.y), I.rot_hi, I.rot_lo, ow + 2 * p);
+        const float2 w = rotate(make_float2(t.z, t.w), I.rot_hi, I.rot_lo, ow + 2 * p + 1);
+        t = make_float4(u.x, u.y, w.x, w.y);
+      }
+      __stcs(reinterpret_cast<float4*>(y) + p, t);
+    }
     if ((n_here & 1) && lane == 0) {
       const int p = (n_here - 1) >> 1;
       const float4 t = s4[p ^ ((p >> 3) & 7)];
-      y[n_here - 1] = make_float2(t.x, t.y);
+      y[n_here - 1] = rotate(make_float2(t.x, t.y), I.rot_hi, I.rot_lo, ow + n_here - 1);
     }
   } else {
     for (int p = lane; p < n_here; p += 32) {
       const int f = p >> 1;
       const float4 t = s4[f ^ ((f >> 3) & 7)];
-      y[p] = (p & 1) ? make_float2(t.z, t.w) : make_float2(t.x, t.y);
+      y[p] = rotate((p & 1) ? make_float2(t.z, t.w) : make_float2(t.x, t.y), I.rot_hi, I.rot_lo,
+                    ow + p);
     }
   }
 }
@@ -362,6 +397,12 @@ cudaError_t launch_resample_tiled32(const RsArgs& a, int q, cudaStream_t s) {
   if (q == 8) resample_tiled_kernel<16, 3><<<a.n_tiles, kRsTile / 8, 0, s>>>(a);
   else if (q == 4) resample_tiled_kernel<16, 2><<<a.n_tiles, kRsTile / 4, 0, s>>>(a);
   else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_freqconv(const RsArgs& a, cudaStream_t s) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  freqconv_kernel<<<a.n_tiles, kRsThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -447,7 +488,7 @@ __global__ void __launch_bounds__(256) exact_fp32_kernel(ExArgs a) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int p = p0 + tp * 2 + j;
-      if (p < a.n_pulses) I.y[(size_t)p * a.n_out + n] = acc[i][j];
+      if (p < a.n_pulses) I.y[(size_t)p * a.n_out + n] = rotate(acc[i][j], I.rot_hi, I.rot_lo, n);
     }
   }
 }
@@ -488,8 +529,8 @@ __global__ void __launch_bounds__(256) exact_gemv_kernel(ExArgs a) {
   if (e == 0.f) {                                  // alpha n on a sample: copy it
     if (lane < np) {
       const bool in = mn >= 0 && mn < a.n_in;
-      I.y[(size_t)lane * a.n_out + n] = in ? __ldg(I.x + (size_t)lane * a.n_in + mn)
-                                           : make_float2(0.f, 0.f);
+      const float2 v = in ? __ldg(I.x + (size_t)lane * a.n_in + mn) : make_float2(0.f, 0.f);
+      I.y[(size_t)lane * a.n_out + n] = rotate(v, I.rot_hi, I.rot_lo, n);
     }
     return;
   }
@@ -514,7 +555,7 @@ __global__ void __launch_bounds__(256) exact_gemv_kernel(ExArgs a) {
   if (lane == 0) {
 #pragma unroll
     for (int p = 0; p < P; ++p)
-      if (p < np) I.y[(size_t)p * a.n_out + n] = acc[p];
+      if (p < np) I.y[(size_t)p * a.n_out + n] = rotate(acc[p], I.rot_hi, I.rot_lo, n);
   }
 }
 

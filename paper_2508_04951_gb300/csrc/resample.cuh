@@ -16,6 +16,10 @@ struct RsItem {
   int n_in, n_out;
   float dl_hi, dl_lo;  // delta = alpha - 1 as a double-float
   int tile_begin;      // first kRsTile-output tile of this item in the launch
+  // Output n is multiplied by exp(2 pi i g n), g = rot_hi + rot_lo cycles per
+  // sample (0: no rotation): the carrier term fc (alpha - 1) / fs of a
+  // passband dilation, or the tone of frequency conversion.
+  float rot_hi, rot_lo;
 };
 
 struct RsArgs {
@@ -35,6 +39,7 @@ struct ExItem {
   const float2* x;     // [n_pulses][n_in]
   float2* y;           // [n_pulses][n_out]
   float dl_hi, dl_lo;
+  float rot_hi, rot_lo;  // carrier term, as in RsItem (0: none)
 };
 struct ExArgs {
   const ExItem* items; // one per alpha (grid.z)
@@ -51,6 +56,9 @@ constexpr float kRsQuadSpan = 0.015f;
 inline int resample_q(double delta_abs) { return delta_abs * 255.0 <= 0.98 * kRsQuadSpan ? 8 : 4; }
 
 cudaError_t launch_resample_tiled32(const RsArgs& a, int q, cudaStream_t s);
+// Frequency conversion (Sec. I, Table I): y[n] = x[n] exp(2 pi i g n) for
+// n < n_out, x = 0 beyond n_in; g from the items' rotation fields.
+cudaError_t launch_freqconv(const RsArgs& a, cudaStream_t s);
 cudaError_t launch_resample_direct(const RsArgs& a, cudaStream_t s);
 cudaError_t launch_exact_fp32(const ExArgs& a, int n_alpha, cudaStream_t s);
 

@@ -39,6 +39,21 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def c_layout(exprs):
+    """Evaluate sizeof / offsetof expressions over include/dc.h with the host C
+    compiler."""
+    import tempfile
+    hdr = os.path.join(ROOT, "include")
+    body = "".join(f'  printf("%zu\\n", (size_t)({e}));\n' for e in exprs)
+    src = f"#include <stdio.h>\n#include <stddef.h>\n#include \"dc.h\"\nint main(void) {{\n{body}  return 0;\n}}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "t.c"), os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", hdr, c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    return [int(v) for v in out.split()]
+
+
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True).stdout
     exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
@@ -56,9 +71,13 @@ def test_binding_names_match_header(lib):
     assert set(dcg.exported_symbols()) <= set(declared_functions())
     dcg.load()
     o = dcg.dc_opts_default()
-    assert (o.taps, o.kaiser_beta, o.mode, o.n_out) == (32, 8.0, 0, 0)
+    assert (o.taps, o.kaiser_beta, o.mode, o.n_out, o.carrier_shift, o.freq_ref) == (32, 8.0, 0, 0, 0, 0.0)
     assert dcg.ITEM_DTYPE.itemsize == 64
-    assert ctypes.sizeof(dcg.DcOpts) == 32
+    # the binding's struct layouts are the header's, as a C compiler lays them out
+    sizes = c_layout(["sizeof(dc_opts)", "sizeof(dc_item)", "offsetof(dc_opts, freq_ref)",
+                      "offsetof(dc_opts, carrier_shift)"])
+    assert sizes == [ctypes.sizeof(dcg.DcOpts), dcg.ITEM_DTYPE.itemsize, dcg.DcOpts.freq_ref.offset,
+                     dcg.DcOpts.carrier_shift.offset]
 
 
 def test_status_strings(lib):
