@@ -266,6 +266,31 @@ DC_API dc_status correct_compress_bank(dc_ctx* ctx, const dc_c64* x_dev, long lo
                                        int n_tec, dc_c64* out_dev, double fs, double fc,
                                        const dc_opts* opts, void* stream);
 
+/* Predistorted LFM transmit waveforms: the comparison methods of the paper's
+ * FFT correction (Sec. II-A, Sec. II-C, Appendix B), generated on the GPU.
+ * y_dev[m] = exp(i (phi(t_m) - 2 pi f_mix t_m)), t_m = m / fs, m < n, for an
+ * LFM from f0 over `bandwidth` in T seconds predistorted for the two-way
+ * ionosphere of TEC tec_tecu (K2 = kappa E, Eq. 3):
+ *   DC_LFM_PLAIN          the undistorted LFM, phi = 2 pi (f0 t + B t^2/(2T))
+ *   DC_LFM_CUBIC          f(t) the real root of Eq. 4 (Eqs. 11-14), phi by the
+ *                         trapezoidal rule over the samples
+ *   DC_LFM_POLY           the pseudo-Chebyshev expansion (Eqs. 5-10), phi in
+ *                         closed form
+ *   DC_LFM_POLY_ORIGINAL  the same with the factor-4 coefficients of
+ *                         Appendix B (the paper's negative control)
+ * Phases are carried in FP64 cycles and reduced before the FP32 sincos.
+ * f_mix = 0 gives RF samples; f_mix = f0 gives the baseband sweep 0 .. B.
+ * 1 <= n <= 2^22; fs, f0, bandwidth, T > 0; tec_tecu >= 0 and finite. */
+typedef enum {
+  DC_LFM_PLAIN = 0,
+  DC_LFM_CUBIC = 1,
+  DC_LFM_POLY = 2,
+  DC_LFM_POLY_ORIGINAL = 3
+} dc_lfm_kind;
+DC_API dc_status predistort_lfm(dc_ctx* ctx, dc_c64* y_dev, long long n, double fs, double f0,
+                                double bandwidth, double T, double tec_tecu, double f_mix,
+                                int kind, void* stream);
+
 /* Exact-sinc resampling of many pulses per range rate (Eq. 17 as a dense
  * contraction Y_a = X_a S_a^T, S_a[j][i] = sinc(alpha_a j - i)).
  * x_dev: pulses [n_alpha][n_pulses][n] with x_alpha_stride samples between

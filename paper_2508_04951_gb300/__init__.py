@@ -25,6 +25,7 @@ __all__ = [
     "ITEM_DTYPE", "dc_opts_default", "dc_check", "dc_launch_count", "dc_profile_enable",
     "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc",
     "correct_batch", "correct_bank", "correct_compress", "correct_compress_bank",
+    "predistort_lfm", "DC_LFM_PLAIN", "DC_LFM_CUBIC", "DC_LFM_POLY", "DC_LFM_POLY_ORIGINAL",
     "resample_exact_batch", "exported_symbols",
     "Plan", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute", "dc_plan_launches",
     "dc_plan_destroy", "Server", "dc_serve_start", "dc_serve_submit", "dc_serve_wait",
@@ -32,6 +33,7 @@ __all__ = [
 ]
 
 DC_WINDOWED, DC_EXACT_FP32, DC_EXACT_BF16X3, DC_EXACT_FP16X3, DC_FREQCONV = 0, 1, 2, 3, 4
+DC_LFM_PLAIN, DC_LFM_CUBIC, DC_LFM_POLY, DC_LFM_POLY_ORIGINAL = 0, 1, 2, 3
 STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_EBUSY", 4: "DC_ECUDA",
           5: "DC_ETIMEOUT", 6: "DC_ECANCELLED"}
 
@@ -101,6 +103,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "iono_correct_noalloc": (i, [vp, ll, vp, d, d, d, vp]),
         "correct_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), vp]),
         "correct_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts), vp]),
+        "predistort_lfm": (i, [vp, vp, ll, d, d, d, d, d, d, i, vp]),
         "correct_compress": (i, [vp, vp, ll, vp, ll, vp, d, d, d, d, ctypes.POINTER(DcOpts), vp]),
         "correct_compress_bank": (i, [vp, vp, ll, vp, ll, dp, i, dp, i, vp, d, d,
                                       ctypes.POINTER(DcOpts), vp]),
@@ -137,7 +140,7 @@ def exported_symbols() -> list[str]:
     """Names of the C entry points this binding binds (all declared in dc.h)."""
     return ["dc_opts_default", "dc_status_str", "dc_create", "dc_destroy", "dc_last_error",
             "dc_check", "dc_launch_count", "dc_profile_enable", "dc_profile_read", "doppler_resample", "iono_correct", "iono_correct_noalloc", "correct_batch", "correct_bank",
-            "correct_compress", "correct_compress_bank",
+            "correct_compress", "correct_compress_bank", "predistort_lfm",
             "resample_exact_batch", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute",
             "dc_plan_launches", "dc_plan_destroy", "dc_serve_start", "dc_serve_submit",
             "dc_serve_wait", "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop"]
@@ -325,6 +328,14 @@ def correct_compress_bank(ctx: Context, x, replica, v_r, tec_tecu, out, fs: floa
                                             replica.numel(), _dptr(v), len(v), _dptr(t), len(t),
                                             _ptr(out, pinned_ok=True), fs, fc, ctypes.byref(o),
                                             _stream(stream)))
+
+
+def predistort_lfm(ctx: Context, y, fs: float, f0: float, bandwidth: float, T: float, tec_tecu: float,
+                   *, f_mix: float = 0.0, kind=DC_LFM_CUBIC, stream=None) -> None:
+    """Fill y (complex64, its length = samples) with a predistorted LFM
+    transmit waveform (kind: DC_LFM_PLAIN / _CUBIC / _POLY / _POLY_ORIGINAL)."""
+    ctx.check(ctx.lib.predistort_lfm(ctx.handle, _ptr(y), y.numel(), fs, f0, bandwidth, T, tec_tecu,
+                                     f_mix, int(kind), _stream(stream)))
 
 
 def resample_exact_batch(ctx: Context, x, n: int, n_pulses: int, v_r, y, *, n_out=0,

@@ -15,6 +15,7 @@
 #include "fft.cuh"
 #include "fused.cuh"
 #include "phase.cuh"
+#include "predist.cuh"
 #include "resample.cuh"
 #include "tma.cuh"
 #include "twiddle_host.h"
@@ -89,11 +90,11 @@ dc_status cuda_fail(dc_ctx* c, cudaError_t e, const char* what) {
 // Kernel phases, named in dc_profile_read().
 enum Ph { PH_RS_TILED, PH_RS_DIRECT, PH_EXACT, PH_ROW_FULL, PH_COL_F1, PH_ROW_MID, PH_COL_B,
           PH_ROW_SPEC, PH_ROW_APPLY, PH_PHASE_TABLE, PH_FUSED_FULL, PH_FUSED_SPEC, PH_FUSED_APPLY,
-          PH_EXACT_TC, PH_FREQCONV, PH_COUNT };
+          PH_EXACT_TC, PH_FREQCONV, PH_PREDIST, PH_COUNT };
 const char* kPhaseName[PH_COUNT] = {"resample_tiled", "resample_direct", "exact_fp32", "row_full",
                                     "col_f1", "row_mid", "col_b", "row_spec", "row_apply",
                                     "phase_table", "fused_full", "fused_spec", "fused_apply",
-                                    "exact_tc", "freqconv"};
+                                    "exact_tc", "freqconv", "predistort_lfm"};
 // Transform lengths handled by the cluster-fused kernels.
 bool fused_L(int log2L) { return log2L >= 12 && log2L <= 16; }
 
@@ -1178,6 +1179,31 @@ extern "C" dc_status correct_compress(dc_ctx* c, const dc_c64* x, long long n,
   it[0].n_valid = (int)n_out;
   it[0].n_out = (int)n_out;
   return run_iono_class(c, it, log2L, T, 1, item_at, s);
+}
+
+extern "C" dc_status predistort_lfm(dc_ctx* c, dc_c64* y, long long n, double fs, double f0,
+                                    double bandwidth, double T, double tec, double f_mix, int kind,
+                                    void* stream) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  if (!y) return fail(c, DC_EINVAL, "null buffer");
+  if (n < 1 || n > (1LL << 22)) return fail(c, DC_EINVAL, "n must be in [1, 2^22], got %lld", n);
+  if (kind < DC_LFM_PLAIN || kind > DC_LFM_POLY_ORIGINAL)
+    return fail(c, DC_EINVAL, "unknown waveform kind %d", kind);
+  if (!(fs > 0.0) || !(f0 > 0.0) || !(bandwidth > 0.0) || !(T > 0.0) || !std::isfinite(fs) ||
+      !std::isfinite(f0) || !std::isfinite(bandwidth) || !std::isfinite(T) || !std::isfinite(f_mix))
+    return fail(c, DC_EINVAL, "fs, f0, bandwidth and T must be finite and > 0");
+  if (!(tec >= 0.0) || !std::isfinite(tec)) return fail(c, DC_EINVAL, "tec must be finite and >= 0");
+  cudaSetDevice(c->device);
+  cudaStream_t s = S(stream);
+  dc_status st;
+  if (kind == DC_LFM_CUBIC && (st = ensure_ws(c, predist_scratch_bytes(n)))) return st;
+  const PredistParams p =
+      predist_params(kind, fs, f0, bandwidth, T, kKappa * tec * 1e16, kC, f_mix);
+  Phase ph(c, PH_PREDIST, s, n);
+  cudaError_t e = launch_predist(p, reinterpret_cast<float2*>(y), n, c->ws, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "predistortion launch");
+  return DC_OK;
 }
 
 extern "C" dc_status resample_exact_batch(dc_ctx* c, const dc_c64* x, long long n, int n_pulses,
