@@ -220,7 +220,13 @@ DC_API dc_status correct_batch(dc_ctx* ctx, const dc_c64* in_dev, dc_c64* out_de
                         const dc_item* items, int n_items, const dc_opts* opts,
                         void* stream);
 
-/* Doppler bank: one pulse corrected for every (v_r, TEC) pair.
+/* Doppler bank: one pulse corrected for every (v_r, TEC) pair.  With
+ * DC_WINDOWED, 32 taps and no carrier term the resampling of all range rates
+ * runs as a tensor-core contraction (Sec. III-B's windowed sum over the
+ * shared input; see dc_tuning.resample_tc) wherever the range rates, ordered
+ * in groups of 32, stay within 30 samples of each other in delay over the
+ * pulse (a group spanning the whole of -8 .. +8 km/s qualifies up to about
+ * 2.6e5 samples); else on CUDA cores.
  * x_dev: [n]; v_r: host [n_v]; tec_tecu: host [n_tec];
  * out_dev: [n_v][n_tec][n_out] (n_out = opts->n_out or n).  Modes DC_WINDOWED
  *          and DC_FREQCONV.
@@ -328,14 +334,21 @@ DC_API dc_status dc_plan_destroy(dc_plan* plan);
  * paper itself processes one pulse per launch).
  *
  * dc_serve_start creates a server on `device` whose scheduler thread keeps up
- * to `slots` batches in flight.  Each slot owns a stream, a context and device
- * buffers carved from `hbm_budget_bytes` (0 = 8 GiB): 48 bytes per sample of
- * batch capacity, at most 32 Mi samples per slot; a slot must hold 2^20
- * samples or the call fails with DC_EINVAL.  Requests are admitted into a free
- * slot in arrival order while they fit its capacity (the HBM admission rule);
- * a slot's batch runs H2D -> correct_batch -> D2H on its stream while the next
- * slot fills with requests that arrived meanwhile.  Results do not depend on
- * the batch a request rode in.
+ * to `slots` batches in flight, each on its own stream and context with its
+ * own pinned host staging.  `hbm_budget_bytes` (0 = 8 GiB) bounds the
+ * server's device memory: 1 MiB per slot is set aside for the slot's context
+ * (tables, item lists) and the rest becomes one pool, allocated at start, from
+ * which every batch in flight takes one block for its inputs, its outputs and
+ * its correction scratch (about 40 bytes per sample), returned when the batch
+ * completes.  The pool must hold a 2^20-sample request alone (32 MiB), else
+ * DC_EINVAL.  Admission: requests join the next free slot's batch in arrival
+ * order while they fit its staging (up to 32 Mi samples) and the pool can
+ * hold the whole batch; a request the pool cannot hold yet waits until
+ * batches in flight return memory (admission by the HBM budget), one that
+ * finds every slot busy waits for a slot.  A slot's batch runs H2D ->
+ * correct_batch -> D2H on its stream while the next slot fills with requests
+ * that arrived meanwhile.  Results do not depend on the batch a request rode
+ * in.
  *
  * dc_serve_submit queues one pulse (x_host: [n] samples, read when the request
  * is admitted; y_host: [n] corrected samples, written before dc_serve_wait
@@ -345,8 +358,9 @@ DC_API dc_status dc_plan_destroy(dc_plan* plan);
  * latency from submission to completion, and forgets it.  dc_serve_cancel
  * drops a request still queued (DC_EBUSY once admitted).  dc_serve_stats
  * reports p50 / p99 latency, completed Msamples/s since the first submission,
- * and the number of completed requests.  dc_serve_stop drains in-flight work
- * and frees the server (requests not yet waited for are dropped). */
+ * and the number of completed requests; dc_serve_counters the admission
+ * counters below.  dc_serve_stop drains in-flight work and frees the server
+ * (requests not yet waited for are dropped). */
 typedef struct dc_server dc_server;
 DC_API dc_status dc_serve_start(int device, size_t hbm_budget_bytes, int slots, const dc_opts* opts,
                                 dc_server** server);
@@ -359,6 +373,18 @@ DC_API dc_status dc_serve_stats(dc_server* server, double* p50_s, double* p99_s,
                                 double* msamples_per_s, long long* completed);
 DC_API dc_status dc_serve_stop(dc_server* server);
 
+typedef struct {
+  long long batches;          /* batches launched                                  */
+  long long completed;        /* requests completed                                */
+  long long waited_memory;    /* requests that, first in line with a slot free,
+                                 waited for the pool (the HBM budget)              */
+  long long waited_slot;      /* requests that, first in line, found every slot busy */
+  size_t pool_bytes;          /* device pool carved from the budget                */
+  size_t peak_bytes_in_flight;/* most pool bytes held by batches at once           */
+  long long batch_capacity;   /* samples a batch may carry (staging)               */
+} dc_serve_info;
+DC_API dc_status dc_serve_counters(dc_server* server, dc_serve_info* out);
+
 /* ----------------------------------------------------------- autotuning
  * Schedule choices of correct_batch / correct_bank (plans record whatever
  * the context holds when they are created):
@@ -367,8 +393,13 @@ DC_API dc_status dc_serve_stop(dc_server* server);
  *   fft[m]      for L = 2^m, 4096 <= L <= 65536: 1 = cluster-fused kernels,
  *               2 = one row pass (L = 4096) or three passes;
  *   chunk[m]    bytes of three-pass intermediate per chunk of transforms of
- *               L = 2^m (-1 = a whole length class at once).
- * 0 in any field means the library's built-in rule. */
+ *               L = 2^m (-1 = a whole length class at once);
+ *   resample_tc the bank's windowed resampling: 1 = tensor cores (a GEMM of
+ *               the pulse's Hankel tiles with per-range-rate tap weights and
+ *               their derivatives, fp16 hi/lo operands; used where the range
+ *               rates allow it), 2 = the CUDA-core kernel.
+ * 0 in any field means the library's built-in rule (tensor cores where
+ * eligible for resample_tc). */
 typedef struct {
   int resample_q;
   int fft[21];
@@ -376,6 +407,7 @@ typedef struct {
   double ms_default;    /* the tuned call under the schedule held before tuning */
   double ms_best;       /* the same call under the chosen schedule              */
   int candidates;       /* schedules timed                                      */
+  int resample_tc;
 } dc_tuning;
 
 /* Measure the schedule choices the call meets on its own data (each

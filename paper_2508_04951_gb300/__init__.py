@@ -29,7 +29,7 @@ __all__ = [
     "resample_exact_batch", "exported_symbols",
     "Plan", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute", "dc_plan_launches",
     "dc_plan_destroy", "Server", "dc_serve_start", "dc_serve_submit", "dc_serve_wait",
-    "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop",
+    "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop", "dc_serve_counters",
 ]
 
 DC_WINDOWED, DC_EXACT_FP32, DC_EXACT_BF16X3, DC_EXACT_FP16X3, DC_FREQCONV = 0, 1, 2, 3, 4
@@ -51,7 +51,15 @@ class DcOpts(ctypes.Structure):
 class DcTuning(ctypes.Structure):
     _fields_ = [("resample_q", ctypes.c_int), ("fft", ctypes.c_int * 21),
                 ("chunk", ctypes.c_longlong * 21), ("ms_default", ctypes.c_double),
-                ("ms_best", ctypes.c_double), ("candidates", ctypes.c_int)]
+                ("ms_best", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("resample_tc", ctypes.c_int)]
+
+
+class DcServeInfo(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("waited_memory", ctypes.c_longlong), ("waited_slot", ctypes.c_longlong),
+                ("pool_bytes", ctypes.c_size_t), ("peak_bytes_in_flight", ctypes.c_size_t),
+                ("batch_capacity", ctypes.c_longlong)]
 
 
 class DcPhaseTime(ctypes.Structure):
@@ -121,6 +129,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "dc_serve_stats": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                ctypes.POINTER(ll)]),
         "dc_serve_stop": (i, [vp]),
+        "dc_serve_counters": (i, [vp, ctypes.POINTER(DcServeInfo)]),
         "dc_autotune_batch": (i, [vp, vp, vp, vp, i, ctypes.POINTER(DcOpts), vp,
                                   ctypes.POINTER(DcTuning)]),
         "dc_autotune_bank": (i, [vp, vp, ll, dp, i, dp, i, vp, d, d, ctypes.POINTER(DcOpts), vp,
@@ -143,7 +152,8 @@ def exported_symbols() -> list[str]:
             "correct_compress", "correct_compress_bank", "predistort_lfm",
             "resample_exact_batch", "dc_plan_batch", "dc_plan_bank", "dc_plan_execute",
             "dc_plan_launches", "dc_plan_destroy", "dc_serve_start", "dc_serve_submit",
-            "dc_serve_wait", "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop"]
+            "dc_serve_wait", "dc_serve_cancel", "dc_serve_stats", "dc_serve_stop",
+            "dc_serve_counters"]
 
 
 # ---------------------------------------------------------------- helpers
@@ -429,6 +439,9 @@ class Server:
     def stop(self):
         dc_serve_stop(self)
 
+    def counters(self) -> dict:
+        return dc_serve_counters(self)
+
     def __del__(self):
         try:
             self.stop()
@@ -490,6 +503,17 @@ def dc_serve_stats(srv: Server) -> dict:
     return {"p50_s": p50.value, "p99_s": p99.value, "msamples_per_s": msps.value, "completed": n.value}
 
 
+def dc_serve_counters(srv: Server) -> dict:
+    """Admission counters: batches, completed, waited_memory (requests held
+    back by the HBM budget), waited_slot, pool_bytes, peak_bytes_in_flight,
+    batch_capacity."""
+    info = DcServeInfo()
+    st = srv.lib.dc_serve_counters(srv.handle, ctypes.byref(info))
+    if st:
+        raise DcError(st, "dc_serve_counters failed")
+    return {f: getattr(info, f) for f, _ in DcServeInfo._fields_}
+
+
 def dc_serve_stop(srv: Server) -> None:
     if getattr(srv, "handle", None):
         srv.lib.dc_serve_stop(srv.handle)
@@ -500,7 +524,7 @@ def dc_serve_stop(srv: Server) -> None:
 # ----------------------------------------------------------- autotuning
 
 def _tuning_dict(t: DcTuning) -> dict:
-    return {"resample_q": t.resample_q,
+    return {"resample_q": t.resample_q, "resample_tc": t.resample_tc,
             "fft": {m: t.fft[m] for m in range(21) if t.fft[m]},
             "chunk": {m: t.chunk[m] for m in range(21) if t.chunk[m]},
             "ms_default": t.ms_default, "ms_best": t.ms_best, "candidates": t.candidates}
@@ -545,6 +569,7 @@ def dc_tuning_set(ctx: Context, schedule: dict | None) -> None:
         return
     t = DcTuning()
     t.resample_q = int(schedule.get("resample_q", 0))
+    t.resample_tc = int(schedule.get("resample_tc", 0))
     for m, v in schedule.get("fft", {}).items():
         t.fft[int(m)] = int(v)
     for m, v in schedule.get("chunk", {}).items():

@@ -14,6 +14,7 @@
 #include "exact_tc.cuh"
 #include "fft.cuh"
 #include "fused.cuh"
+#include "internal.h"
 #include "phase.cuh"
 #include "predist.cuh"
 #include "resample.cuh"
@@ -67,6 +68,7 @@ struct dc_ctx {
     int rs_q = 0;              // outputs per lane of the tiled resampler: 8 or 4
     long long chunk[21] = {};  // three-pass intermediate bytes per chunk (-1: whole class)
     int fft[21] = {};          // 4096 <= L <= 65536: 1 cluster-fused, 2 three passes
+    int rs_tc = 0;             // bank resampling: 1 tensor cores (where eligible), 2 CUDA cores
   } tune;
   std::recursive_mutex mu;
 };
@@ -90,11 +92,11 @@ dc_status cuda_fail(dc_ctx* c, cudaError_t e, const char* what) {
 // Kernel phases, named in dc_profile_read().
 enum Ph { PH_RS_TILED, PH_RS_DIRECT, PH_EXACT, PH_ROW_FULL, PH_COL_F1, PH_ROW_MID, PH_COL_B,
           PH_ROW_SPEC, PH_ROW_APPLY, PH_PHASE_TABLE, PH_FUSED_FULL, PH_FUSED_SPEC, PH_FUSED_APPLY,
-          PH_EXACT_TC, PH_FREQCONV, PH_PREDIST, PH_COUNT };
+          PH_EXACT_TC, PH_FREQCONV, PH_PREDIST, PH_RS_TC, PH_COUNT };
 const char* kPhaseName[PH_COUNT] = {"resample_tiled", "resample_direct", "exact_fp32", "row_full",
                                     "col_f1", "row_mid", "col_b", "row_spec", "row_apply",
                                     "phase_table", "fused_full", "fused_spec", "fused_apply",
-                                    "exact_tc", "freqconv", "predistort_lfm"};
+                                    "exact_tc", "freqconv", "predistort_lfm", "resample_tc"};
 // Transform lengths handled by the cluster-fused kernels.
 bool fused_L(int log2L) { return log2L >= 12 && log2L <= 16; }
 
@@ -417,7 +419,79 @@ dc_status run_windowed(dc_ctx* c, std::vector<RsItem>& items, const dc_opts& o, 
   return DC_OK;
 }
 
+// The bank's resampling on tensor cores (rs_tc.cu): the range rates ordered
+// by delta in groups of 32, each group's integer offsets over a 128-output
+// tile spanning at most rs_tc_max_span() samples.  Returns DC_EINVAL, having
+// launched and uploaded nothing, when the range rates are too far apart for
+// that (the caller then takes the CUDA-core kernel); other failures as usual.
+dc_status run_resample_tc(dc_ctx* c, const float2* x, int n_in, int n_out, const double* v_r,
+                          int n_v, const dc_opts& o, float2* Y, size_t item_at, cudaStream_t s) {
+  std::vector<int> order(n_v);
+  std::vector<double> dl(n_v);
+  for (int i = 0; i < n_v; ++i) {
+    order[i] = i;
+    dl[i] = alpha_minus_one(v_r[i]);
+  }
+  std::sort(order.begin(), order.end(), [&](int p, int q) { return dl[p] < dl[q]; });
+  for (int g = 0; g < n_v; g += 32) {
+    const int last = std::min(n_v, g + 32) - 1;
+    const double spread = (dl[order[last]] - dl[order[g]]) * ((double)n_out + 64.0) + 2.0;
+    if (spread > (double)rs_tc_max_span()) return DC_EINVAL;
+  }
+  const std::vector<float> wp = window_poly(o.taps, o.kaiser_beta);
+  std::vector<float> dls(2 * (size_t)n_v);
+  std::vector<int> vidx(n_v);
+  for (int i = 0; i < n_v; ++i) {
+    split(dl[order[i]], dls[2 * i], dls[2 * i + 1]);
+    vidx[i] = order[i];
+  }
+  const float* dwp = nullptr;
+  const float* ddl = nullptr;
+  const int* dvi = nullptr;
+  dc_status st = upload(c, wp, item_at, s, &dwp);
+  if (st) return st;
+  item_at += (wp.size() * sizeof(float) + 255) & ~(size_t)255;
+  if ((st = upload(c, dls, item_at, s, &ddl))) return st;
+  item_at += (dls.size() * sizeof(float) + 255) & ~(size_t)255;
+  if ((st = upload(c, vidx, item_at, s, &dvi))) return st;
+  RsTcArgs a{x, n_in, n_out, Y, ddl, dvi, n_v, dwp, c->err};
+  Phase ph(c, PH_RS_TC, s, (long long)n_v * n_out);
+  cudaError_t e = launch_resample_tc(a, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core resample launch");
+  return DC_OK;
+}
+
 size_t items_bytes_for(size_t n) { return ((n * 128 + 255) & ~(size_t)255) + 16384; }
+
+// Scratch layout of one correct_batch call: the resampled pulse of each item,
+// then per length class 2^13..2^20 on the three-pass schedule the four-step
+// intermediate of `class_chunk` transforms.  Items grouped by L.
+struct BatchLayout {
+  std::vector<size_t> yoff;
+  std::vector<std::vector<int>> by_L;
+  std::vector<size_t> class_T, class_chunk;
+  size_t bytes = 0;
+};
+BatchLayout batch_layout(const dc_ctx* c, const dc_item* items, int n_items) {
+  BatchLayout b;
+  Arena ar;
+  b.yoff.resize(n_items);
+  b.by_L.resize(21);
+  for (int i = 0; i < n_items; ++i) {
+    const long long no = items[i].n_out ? items[i].n_out : items[i].n;
+    b.yoff[i] = ar.take((size_t)no * sizeof(float2));
+    b.by_L[log2_ceil(no)].push_back(i);
+  }
+  b.class_T.assign(21, 0);
+  b.class_chunk.assign(21, 1);
+  for (int m = 13; m <= 20; ++m)
+    if (!b.by_L[m].empty() && !use_fused(c, m)) {
+      b.class_chunk[m] = chunk_items(c, m, b.by_L[m].size(), 0);
+      b.class_T[m] = ar.take(b.class_chunk[m] * ((size_t)1 << m) * sizeof(float2));
+    }
+  b.bytes = ar.off;
+  return b;
+}
 
 // ------------------------------------------------------ correction pipeline
 // One L class of pulses already resampled into y; writes corrected outputs.
@@ -748,25 +822,12 @@ dc_status correct_batch(dc_ctx* c, const dc_c64* in, dc_c64* out, const dc_item*
   const float2* X = reinterpret_cast<const float2*>(in);
   float2* Y = reinterpret_cast<float2*>(out);
 
-  // Scratch: resampled y per item, then four-step T per item of L > 4096.
-  Arena ar;
-  std::vector<size_t> yoff(n_items), toff(n_items, 0);
-  std::vector<int> log2L(n_items);
-  for (int i = 0; i < n_items; ++i) {
-    const long long no = items[i].n_out ? items[i].n_out : items[i].n;
-    yoff[i] = ar.take((size_t)no * sizeof(float2));
-    log2L[i] = log2_ceil(no);
-  }
-  // Group by L.
-  std::vector<std::vector<int>> by_L(21);
-  for (int i = 0; i < n_items; ++i) by_L[log2L[i]].push_back(i);
-  std::vector<size_t> class_T(21, 0), class_chunk(21, 1);
-  for (int m = 13; m <= 20; ++m)
-    if (!by_L[m].empty() && !use_fused(c, m)) {
-      class_chunk[m] = chunk_items(c, m, by_L[m].size(), 0);
-      class_T[m] = ar.take(class_chunk[m] * ((size_t)1 << m) * sizeof(float2));
-    }
-  if ((st = ensure_ws(c, ar.off))) return st;
+  const BatchLayout lay = batch_layout(c, items, n_items);
+  const std::vector<size_t>& yoff = lay.yoff;
+  const std::vector<std::vector<int>>& by_L = lay.by_L;
+  const std::vector<size_t>& class_T = lay.class_T;
+  const std::vector<size_t>& class_chunk = lay.class_chunk;
+  if ((st = ensure_ws(c, lay.bytes))) return st;
   if ((st = ensure_items(c, items_bytes_for((size_t)n_items * 4)))) return st;
   char* ws = c->ws;
   size_t item_at = 0;
@@ -987,8 +1048,14 @@ dc_status bank_impl(dc_ctx* c, const dc_c64* x, long long n, const dc_c64* rep, 
     split(dl, rs[i].dl_hi, rs[i].dl_lo);
     split(rotation_rate(o, dl, fs, fc), rs[i].rot_hi, rs[i].rot_lo);
   }
-  if ((st = run_windowed(c, rs, o, item_at, s))) return st;
-  item_at += 2 * ((n_v * sizeof(RsItem) + 255) & ~(size_t)255) + 4096;
+  const bool tc_ok = o.mode == DC_WINDOWED && o.taps == 32 && !o.carrier_shift && c->tune.rs_tc != 2;
+  st = tc_ok ? run_resample_tc(c, reinterpret_cast<const float2*>(x), (int)n, (int)n_out, v_r, n_v, o,
+                               Yr, item_at, s)
+             : DC_EINVAL;
+  if (st == DC_EINVAL) st = run_windowed(c, rs, o, item_at, s);   // not eligible: CUDA cores
+  if (st) return st;
+  item_at += 2 * ((n_v * sizeof(RsItem) + 255) & ~(size_t)255) + 4096 +
+             ((n_v * 3 * sizeof(float) + 32 * 8 * sizeof(float) + 3 * 255) & ~(size_t)255);
   // 2. spectra per v_r (and of the zero-padded replica): four-step layout
   // for L > 4096, natural order below
   std::vector<FftItem> sp(n_sp);
@@ -1401,18 +1468,20 @@ extern "C" dc_status dc_plan_destroy(dc_plan* p) {
 namespace {
 
 struct Choice {
-  int kind;   // 0 resample_q, 1 fft[m], 2 chunk[m]
+  int kind;   // 0 resample_q, 1 fft[m], 2 chunk[m], 3 bank resampling engine
   int m;
   std::vector<long long> values;
 };
 
 long long tune_get(const dc_ctx* c, const Choice& d) {
+  if (d.kind == 3) return c->tune.rs_tc;
   if (d.kind == 0) return c->tune.rs_q;
   if (d.kind == 1) return c->tune.fft[d.m];
   return c->tune.chunk[d.m];
 }
 void tune_set(dc_ctx* c, const Choice& d, long long v) {
-  if (d.kind == 0) c->tune.rs_q = (int)v;
+  if (d.kind == 3) c->tune.rs_tc = (int)v;
+  else if (d.kind == 0) c->tune.rs_q = (int)v;
   else if (d.kind == 1) c->tune.fft[d.m] = (int)v;
   else c->tune.chunk[d.m] = v;
 }
@@ -1443,6 +1512,7 @@ dc_status time_call(dc_ctx* c, F& call, cudaStream_t s, double& ms) {
 void tuning_out(const dc_ctx* c, dc_tuning* t) {
   *t = dc_tuning{};
   t->resample_q = c->tune.rs_q;
+  t->resample_tc = c->tune.rs_tc;
   for (int m = 0; m <= 20; ++m) {
     t->fft[m] = c->tune.fft[m];
     t->chunk[m] = c->tune.chunk[m];
@@ -1551,6 +1621,7 @@ extern "C" dc_status dc_autotune_bank(dc_ctx* c, const dc_c64* x, long long n, c
   bool q8 = false;
   for (int i = 0; i < n_v; ++i)
     if (std::fabs(v_r[i]) < kC) q8 |= resample_q(std::fabs(alpha_minus_one(v_r[i]))) == 8;
+  if (o.mode == DC_WINDOWED && o.taps == 32 && !o.carrier_shift) ch.push_back({3, 0, {1, 2}});
   if (o.mode == DC_WINDOWED && o.taps == 32 && q8) ch.push_back({0, 0, {8, 4}});
   class_choices(ch, log2_ceil(n_out), (size_t)n_v * n_tec);
   cudaSetDevice(c->device);
@@ -1575,15 +1646,42 @@ extern "C" dc_status dc_tuning_set(dc_ctx* c, const dc_tuning* t) {
   }
   if (t->resample_q != 0 && t->resample_q != 4 && t->resample_q != 8)
     return fail(c, DC_EINVAL, "resample_q must be 0, 4 or 8");
+  if (t->resample_tc < 0 || t->resample_tc > 2)
+    return fail(c, DC_EINVAL, "resample_tc must be 0, 1 or 2");
   for (int m = 0; m <= 20; ++m) {
     if (t->fft[m] < 0 || t->fft[m] > 2 || (t->fft[m] && (m < 12 || m > 16)))
       return fail(c, DC_EINVAL, "fft[%d] must be 0, 1 or 2 (and 0 outside 4096 <= L <= 65536)", m);
     if (t->chunk[m] < -1) return fail(c, DC_EINVAL, "chunk[%d] must be >= -1", m);
   }
   c->tune.rs_q = t->resample_q;
+  c->tune.rs_tc = t->resample_tc;
   for (int m = 0; m <= 20; ++m) {
     c->tune.fft[m] = t->fft[m];
     c->tune.chunk[m] = t->chunk[m];
   }
   return DC_OK;
+}
+
+// ------------------------------------------------- internal (serve loop)
+// Scratch bytes a correct_batch call with these items needs on this context,
+// and the call run with caller-provided scratch (the serving loop carves both
+// from its HBM pool, so admission can account for every byte a batch uses).
+size_t dc_internal_batch_scratch(dc_ctx* c, const dc_item* items, int n_items) {
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  return batch_layout(c, items, n_items).bytes;
+}
+
+dc_status dc_internal_correct_batch_ws(dc_ctx* c, const dc_c64* in, dc_c64* out,
+                                       const dc_item* items, int n_items, const dc_opts* opts,
+                                       void* stream, void* ws, size_t ws_bytes) {
+  if (!c) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  char* ws0 = c->ws;
+  const size_t b0 = c->ws_bytes;
+  c->ws = static_cast<char*>(ws);
+  c->ws_bytes = ws_bytes;
+  const dc_status st = correct_batch(c, in, out, items, n_items, opts, stream);
+  c->ws = ws0;
+  c->ws_bytes = b0;
+  return st;
 }

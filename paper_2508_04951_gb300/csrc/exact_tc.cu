@@ -31,7 +31,7 @@
 #include <algorithm>
 
 #include "exact_tc.cuh"
-#include "tma.cuh"
+#include "tc.cuh"
 
 namespace dc {
 
@@ -57,61 +57,9 @@ template <bool FP16> struct Cfg {
 };
 constexpr float kInvPi = 0.318309886183790672f;
 
-DC_DEV void bar_arrive(unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-DC_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-DC_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-DC_DEV void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 64 B =
-// 32 16-bit elements, the 16-byte chunk index XOR-ed with (row >> 1) & 3),
-// 8-row groups 512 B apart (stride byte offset), descriptor version 1.
-DC_DEV uint64_t sw64_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) |
-         ((uint64_t)(512u >> 4) << 32) | ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
-}
-
-// Instruction descriptor, kind::f16: D f32, A/B bf16 (or f16), both K-major,
-// N = 256, M = 128.
+// Instruction descriptor of this kernel's MMAs: N = 256, M = 128.
 template <bool FP16> __host__ __device__ constexpr uint32_t instr_desc() {
-  return (1u << 4) | ((FP16 ? 0u : 1u) << 7) | ((FP16 ? 0u : 1u) << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(kHalfRows >> 4) << 24);
-}
-
-DC_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-DC_DEV void mma_commit(unsigned long long* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_addr(bar))
-               : "memory");
-}
-
-DC_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
-
-DC_DEV void tmem_ld16(uint32_t taddr, float (&f)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-      " [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(r[i]);
+  return f16_instr_desc(!FP16, kHalfRows, BN);
 }
 
 // Split 8 floats into 8 hi and 8 lo 16-bit values (one 16-byte chunk each).
@@ -276,14 +224,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int k8 = cbase + q;              // 16-byte chunk of the 64-byte row
         float v[8];
         const int m0 = kc * BK + k8 * 8;
-        const float d0 = (float)(mn - m0) + en;     // (m_n - m) + e_n at i = 0; exact steps of -1
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int m = m0 + i;
           float val = 0.f;
           if (m < a.n_in) {
+            // (m_n - m) + e_n: the integer part converted exactly, then e_n
+            // added once, so the denominator near m = m_n is e_n itself even
+            // when e_n is far below the rounding unit of the chunk's offset
             if (en == 0.f) val = (m == mn) ? 1.f : 0.f;
-            else val = __fdividef((i & 1) ? -sg : sg, d0 - (float)i);
+            else val = __fdividef((i & 1) ? -sg : sg, exact_i2f(mn - m) + en);
           }
           v[i] = val;
         }

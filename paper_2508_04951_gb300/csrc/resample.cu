@@ -24,25 +24,6 @@ namespace dc {
 constexpr float kInvPi = 0.318309886183790672f;
 constexpr int kRsThreads = 256;
 
-// delta * fi = fl + e with fl integer and e in [0, 1), fi a float holding an
-// integer or half-integer output position (exact), delta a double-float.
-DC_DEV void rs_delay(float dl_hi, float dl_lo, float fi, int& fl, float& e) {
-  df p = two_prod(dl_hi, fi);
-  const float lo = fmaf(dl_lo, fi, p.lo);
-  float f = floorf(p.hi);
-  float r = __fadd_rn(__fsub_rn(p.hi, f), lo);      // p.hi - f is exact
-  if (r < 0.f) {
-    r = __fadd_rn(r, 1.f);
-    f -= 1.f;
-    if (r >= 1.f) { r = 0.f; f += 1.f; }
-  } else if (r >= 1.f) {
-    r = __fsub_rn(r, 1.f);
-    f += 1.f;
-  }
-  fl = (int)f;
-  e = r;
-}
-
 // w(e - k) from the per-tap polynomial, t = k + R - 1.
 DC_DEV float window_at(const float* __restrict__ wp, int t, float e) {
   const float4 lo = __ldg(reinterpret_cast<const float4*>(wp + t * kWCoef));

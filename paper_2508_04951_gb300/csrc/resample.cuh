@@ -46,6 +46,44 @@ struct ExArgs {
   int n_in, n_out, n_pulses;
 };
 
+// delta * fi = fl + e with fl integer and e in [0, 1), fi a float holding an
+// integer or half-integer output position (exact), delta a double-float.
+DC_DEV void rs_delay(float dl_hi, float dl_lo, float fi, int& fl, float& e) {
+  df p = two_prod(dl_hi, fi);
+  const float lo = fmaf(dl_lo, fi, p.lo);
+  float f = floorf(p.hi);
+  float r = __fadd_rn(__fsub_rn(p.hi, f), lo);      // p.hi - f is exact
+  if (r < 0.f) {
+    r = __fadd_rn(r, 1.f);
+    f -= 1.f;
+    if (r >= 1.f) { r = 0.f; f += 1.f; }
+  } else if (r >= 1.f) {
+    r = __fsub_rn(r, 1.f);
+    f += 1.f;
+  }
+  fl = (int)f;
+  e = r;
+}
+
+// One launch of the tensor-core bank resampler (rs_tc.cu): one pulse x[n_in]
+// for n_slots range rates, slot s holding delta = dl[2s] + dl[2s+1] and
+// writing y + vidx[s] * n_out (vidx < 0: an empty slot).  Slots are grouped
+// 32 per CTA; within a group the range rates' integer offsets
+// floor(delta n) over any 128-output tile must span at most
+// rs_tc_max_span() samples (the host orders the slots by delta and checks).
+struct RsTcArgs {
+  const float2* x;
+  int n_in, n_out;
+  float2* y;
+  const float* dl;
+  const int* vidx;
+  int n_slots;
+  const float* wpoly;  // 32-tap window polynomials, as RsArgs::wpoly
+  int* err;
+};
+int rs_tc_max_span();
+cudaError_t launch_resample_tc(const RsTcArgs& a, cudaStream_t s);
+
 constexpr int kRsTile = 1024;     // outputs per CTA of the resampling kernels
 constexpr float kRsTiledMaxDelta = 0.01f;
 // The tiled kernel's warp tile is 32 q outputs (q = 8 or 4 per lane); its

@@ -100,3 +100,21 @@ def test_split_precision_config4_sampled(dcg, ctx):
             ref = oracle.resample_exact_rows(X[p].astype(np.complex128), oracle.alpha(v[i]), rows)
             got = Y[i, p].cpu().numpy().astype(np.complex128)[rows]
             assert rel(got, ref) <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("mode_name", ["DC_EXACT_BF16X3", "DC_EXACT_FP16X3"])
+def test_split_precision_tiny_range_rates(dcg, ctx, mode_name):
+    # |v_r| of metres per second: alpha n sits within 1e-6 of an integer
+    # for thousands of outputs, where the sinc row is one near-1 term and
+    # tiny neighbours; the denominators (m_n - m) + e_n must keep e_n
+    mode = getattr(dcg, mode_name)
+    n, P = 4096, 8
+    v = np.array([4.07, -0.5, 0.01, 7500.0])
+    X = pulses(P * len(v), n, salt=77)
+    Y = run(dcg, ctx, X, n, P, v, n, mode, True)
+    assert np.all(np.isfinite(Y))
+    X64 = X.astype(np.complex128).reshape(len(v), P, n)
+    for i in range(len(v)):
+        ref = oracle.resample_exact(X64[i], oracle.alpha(v[i]), n)
+        for p in (0, P - 1):
+            assert rel(Y[i, p], ref[p]) <= TOL_SPLIT, (v[i], p)
