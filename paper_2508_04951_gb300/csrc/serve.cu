@@ -2,29 +2,35 @@
 //
 // Requests (host pulses with their own fs, fc, v_r and TEC) are queued by
 // dc_serve_submit.  One scheduler thread owns `slots` batch slots, each with
-// its own stream, context (so scratch is never shared between batches in
-// flight), device in/out buffers and pinned staging, all sized from the HBM
-// budget at start.  Whenever a slot is free and requests wait, the scheduler
-// admits queued requests into it in arrival order while they fit its sample
-// capacity, copies their samples into pinned staging, and enqueues
-// H2D -> correct_batch -> D2H -> event on the slot's stream; it does not wait
-// for the GPU, so the next slot fills with requests that arrive meanwhile and
-// batches overlap on the device.  Completed slots (event query) hand results
-// back to the callers' buffers and record the latency from submission to
-// completion.  Each request's result does not depend on which batch it rode in
-// (correct_batch's per-item independence).
+// its own stream, context and pinned staging.  The device memory of every
+// batch in flight -- its input, its output and correct_batch's scratch --
+// comes from one pool carved from the HBM budget at start (first fit, freed
+// when the batch completes).  Whenever a slot is free and requests wait, the
+// scheduler admits queued requests into it in arrival order while they fit
+// the slot's staging and the pool can hold the batch; a request that the
+// pool cannot hold yet waits for in-flight batches to finish (admission by
+// HBM budget), one that finds every slot busy waits for a slot.  A launched
+// batch runs H2D -> correct_batch -> D2H -> event on the slot's stream; the
+// scheduler does not wait for the GPU, so the next slot fills with requests
+// that arrive meanwhile and batches overlap on the device.  Completed slots
+// (event query) hand results back to the callers' buffers, return their pool
+// block and record the latency from submission to completion.  Each
+// request's result does not depend on which batch it rode in (correct_batch's
+// per-item independence).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
 #include <vector>
 
 #include "../../include/dc.h"
+#include "internal.h"
 
 namespace {
 
@@ -39,20 +45,75 @@ struct Request {
   Clock::time_point t_submit, t_done;
   int state = 0;          // 0 queued, 1 in flight, 2 done, 3 failed, 4 cancelled
   dc_status status = DC_OK;
+  bool waited_memory = false, waited_slot = false;
 };
 
 struct Slot {
   dc_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  dc_c64* in_dev = nullptr;
-  dc_c64* out_dev = nullptr;
   dc_c64* in_host = nullptr;    // pinned
   dc_c64* out_host = nullptr;   // pinned
-  long long cap = 0;            // samples
+  long long cap = 0;            // samples of staging
+  size_t block = 0, block_bytes = 0;   // this batch's pool block (offset, bytes)
   std::vector<Request*> reqs;
   std::vector<long long> offs;
   bool busy = false;
+};
+
+// First-fit allocator over the device pool (offsets; 256-byte granules).
+class PoolAlloc {
+ public:
+  void reset(size_t bytes) {
+    free_.clear();
+    if (bytes) free_[0] = bytes;
+    total_ = bytes;
+    used_ = peak_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = round(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t at = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[at] = rest;
+      used_ += bytes;
+      peak_ = std::max(peak_, used_);
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = round(bytes);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t total() const { return total_; }
+  size_t largest() const {
+    size_t m = 0;
+    for (const auto& kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
+  size_t peak() const { return peak_; }
+  static size_t round(size_t b) { return (b + 255) & ~(size_t)255; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t total_ = 0, used_ = 0, peak_ = 0;
 };
 
 // Fixed pool of copy threads: parallel memcpy of request samples between
@@ -132,7 +193,10 @@ struct dc_server {
   int device = 0;
   dc_opts opts{};
   std::vector<Slot> slots;
-  long long cap = 0;
+  long long cap = 0;            // samples per batch (staging)
+  char* pool = nullptr;         // device pool: inputs, outputs, scratch of batches in flight
+  PoolAlloc alloc;
+  long long waited_memory = 0, waited_slot = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
@@ -173,20 +237,47 @@ void finish_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
     ++s->completed;
   }
   s->t_last = now;
+  s->alloc.release(sl.block, sl.block_bytes);
   sl.reqs.clear();
   sl.offs.clear();
   sl.busy = false;
   s->cv_done.notify_all();
 }
 
+// Device bytes of a batch: input and output (`samples`, 16-byte aligned
+// offsets) and correct_batch's scratch for its items.
+size_t batch_bytes(Slot& sl, const std::vector<dc_item>& items, long long samples,
+                   size_t* scratch) {
+  *scratch = dc_internal_batch_scratch(sl.ctx, items.data(), (int)items.size());
+  return 2 * PoolAlloc::round((size_t)samples * sizeof(dc_c64)) + *scratch;
+}
+
 // Admit queued requests into a free slot and enqueue its work (called with
-// the lock held; drops it while staging and enqueuing).
+// the lock held; drops it while staging and enqueuing).  Requests join in
+// arrival order while they fit the slot's staging and the pool can hold the
+// whole batch (inputs, outputs, scratch); if even the first cannot be held,
+// it waits for in-flight batches to return memory.
 bool launch_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
   long long used = 0;
+  std::vector<dc_item> items;
+  size_t bytes = 0, scratch = 0;
   while (!s->queue.empty()) {
     Request* r = s->queue.front();
     const long long need = (r->n + 1) & ~1LL;   // keep 16-byte alignment of offsets
     if (used + need > sl.cap) break;
+    items.push_back(dc_item{used, r->n, used, r->n, r->fs, r->fc, r->v_r, r->tec});
+    size_t sc = 0;
+    const size_t b = batch_bytes(sl, items, used + need, &sc);
+    if (PoolAlloc::round(b) > s->alloc.largest()) {   // the HBM budget is the limit now
+      items.pop_back();
+      if (items.empty() && !r->waited_memory) {
+        r->waited_memory = true;
+        ++s->waited_memory;
+      }
+      break;
+    }
+    bytes = b;
+    scratch = sc;
     s->queue.pop_front();
     sl.reqs.push_back(r);
     sl.offs.push_back(used);
@@ -194,23 +285,34 @@ bool launch_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
     r->state = 1;
   }
   if (sl.reqs.empty()) return false;
+  if (!s->alloc.alloc(bytes, &sl.block)) {      // cannot happen: bytes <= largest free block
+    for (auto it = sl.reqs.rbegin(); it != sl.reqs.rend(); ++it) {
+      (*it)->state = 0;
+      s->queue.push_front(*it);
+    }
+    sl.reqs.clear();
+    sl.offs.clear();
+    return false;
+  }
+  sl.block_bytes = bytes;
   sl.busy = true;
   lk.unlock();
-  std::vector<dc_item> items(sl.reqs.size());
   std::vector<CopyPool::Job> jobs;
-  for (size_t i = 0; i < sl.reqs.size(); ++i) {
-    Request* r = sl.reqs[i];
-    jobs.push_back({sl.in_host + sl.offs[i], r->x, (size_t)r->n * sizeof(dc_c64)});
-    items[i] = dc_item{sl.offs[i], r->n, sl.offs[i], r->n, r->fs, r->fc, r->v_r, r->tec};
-  }
+  for (size_t i = 0; i < sl.reqs.size(); ++i)
+    jobs.push_back({sl.in_host + sl.offs[i], sl.reqs[i]->x, (size_t)sl.reqs[i]->n * sizeof(dc_c64)});
   s->copies->run(jobs);
+  char* base = s->pool + sl.block;
+  const size_t io = PoolAlloc::round((size_t)used * sizeof(dc_c64));
+  dc_c64* in_dev = reinterpret_cast<dc_c64*>(base);
+  dc_c64* out_dev = reinterpret_cast<dc_c64*>(base + io);
   dc_status st = DC_OK;
-  if (cudaMemcpyAsync(sl.in_dev, sl.in_host, (size_t)used * sizeof(dc_c64), cudaMemcpyHostToDevice,
+  if (cudaMemcpyAsync(in_dev, sl.in_host, (size_t)used * sizeof(dc_c64), cudaMemcpyHostToDevice,
                       sl.stream) != cudaSuccess)
     st = DC_ECUDA;
-  if (!st) st = correct_batch(sl.ctx, sl.in_dev, sl.out_dev, items.data(), (int)items.size(), &s->opts,
-                              sl.stream);
-  if (!st && cudaMemcpyAsync(sl.out_host, sl.out_dev, (size_t)used * sizeof(dc_c64),
+  if (!st)
+    st = dc_internal_correct_batch_ws(sl.ctx, in_dev, out_dev, items.data(), (int)items.size(),
+                                      &s->opts, sl.stream, base + 2 * io, scratch);
+  if (!st && cudaMemcpyAsync(sl.out_host, out_dev, (size_t)used * sizeof(dc_c64),
                              cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
     st = DC_ECUDA;
   if (!st && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = DC_ECUDA;
@@ -222,6 +324,7 @@ bool launch_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
       r->status = st;
       r->t_done = now;
     }
+    if (cudaStreamSynchronize(sl.stream) == cudaSuccess) s->alloc.release(sl.block, sl.block_bytes);
     sl.reqs.clear();
     sl.offs.clear();
     sl.busy = false;
@@ -242,10 +345,18 @@ void scheduler(dc_server* s) {
         finish_slot(s, sl, lk);
         progress = true;
       }
+    bool any_free = false;
     for (Slot& sl : s->slots)
       if (!sl.busy && !s->queue.empty()) progress |= launch_slot(s, sl, lk);
     bool any_busy = false;
-    for (Slot& sl : s->slots) any_busy |= sl.busy;
+    for (Slot& sl : s->slots) {
+      any_busy |= sl.busy;
+      any_free |= !sl.busy;
+    }
+    if (!any_free && !s->queue.empty() && !s->queue.front()->waited_slot) {
+      s->queue.front()->waited_slot = true;     // every slot busy: waits for a slot
+      ++s->waited_slot;
+    }
     if (s->stop && !any_busy) break;
     if (!progress) {
       // nothing to do right now: sleep until a submission, or poll the GPU
@@ -268,24 +379,35 @@ extern "C" dc_status dc_serve_start(int device, size_t hbm_budget_bytes, int slo
   s->device = device;
   dc_opts_default(&s->opts);
   if (opts) s->opts = *opts;
-  // Per slot: in + out buffers (16 B/sample) plus correct_batch scratch
-  // (resampled copy and, for L > 65536, a four-step buffer of up to 2x):
-  // budget 48 B per sample of capacity, at most kSlotMax samples per batch.
+  // The budget holds one device pool for the batches in flight (inputs,
+  // outputs, correct_batch scratch) less a fixed reserve per slot for its
+  // context's tables and item lists.  The pool must hold one 2^20-sample
+  // request alone: 16 MiB in and out, 8 MiB resampled, 8 MiB four-step.
   constexpr long long kSlotMax = 32LL << 20;
+  constexpr size_t kSlotReserve = (size_t)1 << 20;
+  constexpr size_t kMinPool = ((size_t)32 << 20) + ((size_t)1 << 16);
   const size_t budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)8 << 30);
-  s->cap = std::min<long long>((long long)(budget / slots / 48), kSlotMax);
-  if (s->cap < (1LL << 20)) {
+  if (budget < (size_t)slots * kSlotReserve + kMinPool) {
     delete s;
-    return DC_EINVAL;            // each slot must hold the largest pulse (2^20 samples)
+    return DC_EINVAL;            // the pool must hold the largest pulse (2^20 samples)
   }
+  const size_t pool = (budget - (size_t)slots * kSlotReserve) & ~(size_t)255;
+  s->cap = std::min<long long>((long long)(pool / (2 * sizeof(dc_c64))), kSlotMax);
+  if (cudaMalloc(&s->pool, pool) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return DC_ENOMEM;
+  }
+  s->alloc.reset(pool);
   s->slots.resize(slots);
   for (Slot& sl : s->slots) {
     sl.cap = s->cap;
     const size_t bytes = (size_t)sl.cap * sizeof(dc_c64);
-    if (dc_create(&sl.ctx, device, (size_t)sl.cap * 32) != DC_OK ||
+    // the context's own scratch is never used (batches take theirs from the
+    // pool), so its cap is one byte: any attempt to allocate fails loudly
+    if (dc_create(&sl.ctx, device, 1) != DC_OK ||
         cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc(&sl.in_dev, bytes) != cudaSuccess || cudaMalloc(&sl.out_dev, bytes) != cudaSuccess ||
         cudaMallocHost(&sl.in_host, bytes) != cudaSuccess ||
         cudaMallocHost(&sl.out_host, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -396,12 +518,24 @@ extern "C" dc_status dc_serve_stop(dc_server* s) {
     if (sl.ctx) dc_destroy(sl.ctx);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.stream) cudaStreamDestroy(sl.stream);
-    if (sl.in_dev) cudaFree(sl.in_dev);
-    if (sl.out_dev) cudaFree(sl.out_dev);
     if (sl.in_host) cudaFreeHost(sl.in_host);
     if (sl.out_host) cudaFreeHost(sl.out_host);
   }
+  if (s->pool) cudaFree(s->pool);
   for (auto& kv : s->reqs) delete kv.second;
   delete s;
+  return DC_OK;
+}
+
+extern "C" dc_status dc_serve_counters(dc_server* s, dc_serve_info* out) {
+  if (!s || !out) return DC_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  out->batches = s->batches;
+  out->completed = s->completed;
+  out->waited_memory = s->waited_memory;
+  out->waited_slot = s->waited_slot;
+  out->pool_bytes = s->alloc.total();
+  out->peak_bytes_in_flight = s->alloc.peak();
+  out->batch_capacity = s->cap;
   return DC_OK;
 }

@@ -138,3 +138,31 @@ def test_serve_rejects_cancels_and_times_out(dcg):
             srv.wait(ids[-1], 1000)
         assert e.value.status == 6
     srv.stop()
+
+
+def test_serve_admission_waits_for_the_hbm_budget(dcg):
+    # 8 slots but a budget whose pool holds two 700k-sample requests at once
+    # (each ~25 MB: input, output, resampled copy, four-step scratch): the
+    # third waits for memory although slots are free, and no more than the
+    # pool is ever in use
+    budget = 8 * (1 << 20) + 60 * (1 << 20)
+    srv = dcg.dc_serve_start(0, budget, slots=8)
+    reqs = [(noise(700000, 300 + k), -8000.0 + 4000 * k, 20.0 + 30 * k) for k in range(4)]
+    outs = [np.zeros_like(x) for x, _, _ in reqs]
+    ids = [srv.submit(x, outs[k], 20e6, 1e9, v, t) for k, (x, v, t) in enumerate(reqs)]
+    for i in ids:
+        srv.wait(i, 60000)
+    c = srv.counters()
+    srv.stop()
+    assert c["completed"] == 4
+    assert c["waited_memory"] >= 1
+    assert c["pool_bytes"] <= budget and 0 < c["peak_bytes_in_flight"] <= c["pool_bytes"]
+    for k, (x, v, t) in enumerate(reqs):
+        ref = oracle.correct(x.astype(np.complex128), 20e6, 1e9, v, t)
+        assert np.linalg.norm(outs[k] - ref) / np.linalg.norm(ref) <= 1e-5, k
+
+
+def test_serve_budget_too_small_for_a_full_pulse(dcg):
+    with pytest.raises(dcg.DcError) as e:
+        dcg.dc_serve_start(0, 16 << 20, slots=2)
+    assert e.value.status == 1
