@@ -21,6 +21,19 @@ Reported (one JSON line on rank 0):
   cpu_baseline  the FP64 oracle on a bounded sample of the same bank
   error       max relative L2 error of the GPU result vs that oracle sample
 
+By default (``--workload all``, one GPU) the line also carries
+``workloads``: one record per other configuration, each with its own clocks,
+error against the oracle, plain-path and CPU baselines and, where one kernel
+dominates, its roofline --
+  plain          one LFM pulse (N = 4096) corrected by a replayed graph, windowed
+                 and exact-sinc; device and host latency p50 / p99
+  batch          4096 ragged pulses (1024 .. 262144 samples) as one graph replay
+  split          exact sinc as a tensor-core contraction: 64 range rates x 512
+                 distinct pulses x N = 8192, bf16 hi/lo operands
+  serve          a Poisson stream (20 k pulses/s, 2048 .. 2^20 samples) through
+                 the continuous-batching server for --duration seconds
+  compress_bank  the bank with pulse compression bundled into its factor tables
+
 ``--impl reference`` times the oracle itself (the method's plain FP64 CPU
 statement) on a bounded sample per step, on the same metric.
 """
@@ -49,10 +62,10 @@ METRIC = "corrected Msamples/s and p50/p99 pulse latency vs plain path at stated
 UNIT = "Msamples/s"
 ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
 # DRAM bytes (read + write) per launch of the kernel at the full workload, from
-# one ncu capture of the reduced 32-range-rate launch (233.0 MB), scaled by the
-# 8x units of the full launch.  Cleared whenever the kernel changes after the
-# capture.
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 8 * 232.981e6}
+# one ncu capture of the full-size launch (dram__bytes_read.sum 146.58 MB +
+# dram__bytes_write.sum 2.09 GB).  Cleared whenever the kernel changes after
+# the capture.
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 146.58e6 + 2.09e9}
 
 
 def load_peaks() -> tuple[float, str]:
@@ -384,19 +397,18 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                           f"{cfg.n_tec} TECs x {cfg.n} samples, {wall:.1f} s"}
         result["error"] = {"rel_l2_max": float(errs.max()), "rel_l2_median": float(np.median(errs)),
                            "pairs_checked": int(errs.size), "tolerance": 1e-5}
-    if rank == 0:
-        print(json.dumps(result), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+    return result
 
 
 # ------------------------------------------------- split-precision workload
 
-def run_split(args) -> None:
+def run_split(args) -> dict:
     """Exact-sinc resampling as a dense contraction: 64 range rates x 512
-    band-limited noise pulses of N = 8192 (pulses shared by the range rates),
-    bf16 hi/lo split operands on tcgen05, against the FP32 CUDA-core path."""
+    distinct band-limited noise pulses of N = 8192 per range rate, bf16 hi/lo
+    split operands on tcgen05, against the FP32 CUDA-core path."""
     import torch
     import paper_2508_04951_gb300 as dcg
 
@@ -405,8 +417,7 @@ def run_split(args) -> None:
     cfg = synth.SplitPrecisionBank()
     if args.n_v:
         cfg.n_alpha = args.n_v
-    X, v = cfg.draw()
-    X = X.astype(np.complex64)
+    X, v = cfg.draw_distinct()                      # [V][P][n] complex64
     n, P, V = cfg.n, cfg.n_pulses, cfg.n_alpha
     ctx = dcg.Context(0)
     stream = torch.cuda.current_stream()
@@ -415,7 +426,7 @@ def run_split(args) -> None:
     mode = dcg.DC_EXACT_FP16X3 if args.split_mode == "fp16x3" else dcg.DC_EXACT_BF16X3
 
     def step(m):
-        dcg.resample_exact_batch(ctx, xd, n, P, v, yd, mode=m)
+        dcg.resample_exact_batch(ctx, xd, n, P, v, yd, mode=m, x_alpha_stride=P * n)
 
     for _ in range(args.warmup):
         step(mode)
@@ -452,7 +463,7 @@ def run_split(args) -> None:
     for i in range(V):
         for pj, p in enumerate(pulses):
             t0 = time.perf_counter()
-            ref = oracle.resample_exact_rows(X[p].astype(np.complex128), oracle.alpha(v[i]), rows)
+            ref = oracle.resample_exact_rows(X[i, p].astype(np.complex128), oracle.alpha(v[i]), rows)
             t_or += time.perf_counter() - t0
             errs.append(float(np.linalg.norm(Yh[i, pj] - ref) / np.linalg.norm(ref)))
     # FP32 CUDA-core path, one step
@@ -463,7 +474,8 @@ def run_split(args) -> None:
     torch.cuda.synchronize()
     fp32_ms = a.elapsed_time(b)
     pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    peak = float(pk["bf16_tflops_sustained"])
+    peak = float(pk["bf16_tflops"])                 # burst: the kernel runs alone
+    peak_sus = float(pk["bf16_tflops_sustained"])
     kname = "exact_tc"
     k_ms = prof[kname][2] / prof[kname][0]
     issued = 3 * 2.0 * n * (2 * P) * n * V          # three hi/lo products per alpha
@@ -473,15 +485,20 @@ def run_split(args) -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
         "dtype": args.split_mode, "data": "synthetic",
         "config": {"workload": "split_precision", "n": n, "n_alpha": V, "n_pulses": P,
-                   "pulses": "512 band-limited noise pulses shared by the 64 range rates"},
+                   "pulses": f"{P} distinct band-limited noise pulses per range rate",
+                   "l2": f"inputs ({X.nbytes / 2**30:.1f} GiB) and outputs larger than L2"},
         "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
         "clocks": clk,
         "roofline": {"bound": "tensor", "kernel": kname, "unit": "TFLOP/s", "peak": peak,
-                     "peak_source": "measured bf16 sustained",
+                     "peak_source": "measured bf16 burst (the kernel timed alone)",
+                     "achieved": issued / (k_ms / 1e3) / 1e12,
+                     "frac": issued / (k_ms / 1e3) / 1e12 / peak,
                      "achieved_issued": issued / (k_ms / 1e3) / 1e12,
                      "frac_issued": issued / (k_ms / 1e3) / 1e12 / peak,
                      "achieved_algorithmic": algo / (k_ms / 1e3) / 1e12,
                      "frac_algorithmic": algo / (k_ms / 1e3) / 1e12 / peak,
+                     "frac_issued_of_sustained": issued / (k_ms / 1e3) / 1e12 / peak_sus,
+                     "flops_issued_per_step": issued, "flops_algorithmic_per_step": algo,
                      "kernel_ms": k_ms, "phases_ms_per_step": {k: vv[2] / args.steps for k, vv in prof.items()}},
         "fp32_cuda_core": {"ms_per_step": fp32_ms, "value": samples / (fp32_ms / 1e3) / 1e6},
         "error": {"rel_l2_max": max(errs), "rel_l2_median": float(np.median(errs)),
@@ -491,13 +508,13 @@ def run_split(args) -> None:
                          "sample": f"{V} range rates x {len(pulses)} pulses x {len(rows)} output rows "
                                    f"(each a {n}-term FP64 sum), {t_or:.1f} s"},
     }
-    print(json.dumps(line), flush=True)
     ctx.close()
+    return line
 
 
 # ---------------------------------------------------------- uneven batch
 
-def run_batch(args) -> None:
+def run_batch(args) -> dict:
     """4096 pulses, lengths log-uniform in [1024, 262144], half LFM / half
     noise, each with its own v_r and TEC, corrected as one graph launch
     (dc_plan_batch), against the plain per-pulse path."""
@@ -604,9 +621,9 @@ def run_batch(args) -> None:
         "cpu_baseline": {"value": s_or / t_or / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"the {len(errs)} checked pulses ({s_or} samples), {t_or:.1f} s"},
     }
-    print(json.dumps(line), flush=True)
     plan.close()
     ctx.close()
+    return line
 
 
 # ------------------------------------------------------ plain single pulse
@@ -641,7 +658,7 @@ def device_times(torch, stream, fn, count: int, block: int = 250):
     return out, fed
 
 
-def run_plain(args) -> None:
+def run_plain(args) -> dict:
     """One LFM pulse (N = 4096, fs = 10 MHz, B = 5 MHz, fc = 1 GHz, v_r = +7.5
     km/s, TEC = 50 TECU) corrected end to end, windowed and exact-sinc: per
     mode a captured plan (one graph launch) replayed --replays times, each
@@ -735,8 +752,8 @@ def run_plain(args) -> None:
         "latency_ms": {"p50": w["device_ms"]["p50"], "p99": w["device_ms"]["p99"]},
         "clocks": clk, "modes": modes,
     }
-    print(json.dumps(line), flush=True)
     ctx.close()
+    return line
 
 
 # --------------------------------------------------------------- serving
@@ -769,7 +786,7 @@ def _serve_check_one(job):
     return float(np.linalg.norm(y.astype(np.complex128) - ref) / np.linalg.norm(ref)), n
 
 
-def run_serve(args) -> None:
+def run_serve(args) -> dict:
     """Poisson request stream (20 k pulses/s) of mixed LFM / noise pulses,
     lengths log-uniform in [2048, 2^20], through the continuous-batching
     server, against a serial per-request server on the same arrivals; a
@@ -820,6 +837,8 @@ def run_serve(args) -> None:
         kept[i] = np.empty(int(lens[i]), dtype=np.complex64)
         kept[i].fill(0)
     th = threading.Thread(target=submitter)
+    clocks = Clocks(0)
+    clocks.start()
     t_start = time.perf_counter()
     th.start()
     for i in range(nreq):
@@ -831,6 +850,7 @@ def run_serve(args) -> None:
             cond.notify()
     th.join()
     wall = time.perf_counter() - t_start
+    clk = clocks.stop()
     st = srv.stats()
     srv.stop()
     # serial per-request server on the first part of the same stream
@@ -876,7 +896,7 @@ def run_serve(args) -> None:
                    "offered_msamples_per_s": float(lens.sum() / args.duration / 1e6),
                    "budget_bytes": cfg.budget_bytes, "slots": args.slots},
         "latency_ms": {"p50": 1e3 * st["p50_s"], "p99": 1e3 * st["p99_s"]},
-        "completed": st["completed"], "wall_s": wall,
+        "completed": st["completed"], "wall_s": wall, "clocks": clk,
         "plain_path": {"what": "serial per-request correct_batch with synchronous copies",
                        "requests": k_serial,
                        "value": float(lens[:k_serial].sum() / serial_wall / 1e6), "unit": UNIT,
@@ -891,7 +911,127 @@ def run_serve(args) -> None:
         line["cpu_baseline"] = {"value": s_or / t_or / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"the {len(errs)} checked requests ({s_or} samples) on "
                                           f"{cores} spawned processes, {t_or:.1f} s"}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+# ------------------------------------------- bank with pulse compression
+
+def run_compress(args) -> dict:
+    """The Doppler bank compressed against a replica (correct_compress_bank:
+    the matched filter folded into each TEC's factor table) against the plain
+    bank (correct_bank) on the same pulse: the added cost of bundling pulse
+    compression with the correction (Sec. II-B)."""
+    import torch
+    import paper_2508_04951_gb300 as dcg
+    import oracle
+    from oracle import compression as pc
+
+    dcg.build.build()
+    dcg.load()
+    cfg = synth.DopplerBank()
+    if args.n_v:
+        cfg.n_v = args.n_v
+    x, v, tec = cfg.draw()
+    n_rep = 4096
+    h = synth.lfm(n_rep, cfg.fs, 5e6).astype(np.complex64)
+    ctx = dcg.Context(0)
+    stream = torch.cuda.current_stream()
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    hd = torch.from_numpy(h).cuda()
+    n_samples = cfg.n_v * cfg.n_tec * cfg.n
+    out = torch.empty(n_samples, dtype=torch.complex64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    calls = {"compress": lambda: dcg.correct_compress_bank(ctx, xd, hd, v, tec, out, cfg.fs, cfg.fc),
+             "plain": lambda: dcg.correct_bank(ctx, xd, v, tec, out, cfg.fs, cfg.fc)}
+    steps = max(1, args.sub_steps)
+    res = {}
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    for name, fn in calls.items():
+        for _ in range(args.warmup):
+            fn()
+        dcg.dc_check(ctx)
+        dcg.dc_profile_enable(ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k, (a, b) in enumerate(ev):
+            flush.fill_(k & 255)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        prof = dcg.dc_profile_read(ctx)
+        dcg.dc_profile_enable(ctx, False)
+        res[name] = ([a.elapsed_time(b) for a, b in ev], prof)
+    clk = clocks.stop()
+    # the compressed bank's result on sampled pairs and lags vs the oracle
+    calls["compress"]()
+    torch.cuda.synchronize()
+    got = out.view(cfg.n_v, cfg.n_tec, cfg.n)
+    rng = np.random.default_rng(21)
+    lags = np.unique(np.concatenate([np.arange(32), rng.integers(0, cfg.n, 300)]))
+    errs, t_or = [], 0.0
+    x64, h64 = x.astype(np.complex64).astype(np.complex128), h.astype(np.complex128)
+    for i, t in ((0, 0), (cfg.n_v - 1, cfg.n_tec - 1), (cfg.n_v // 2, cfg.n_tec // 3)):
+        t0 = time.perf_counter()
+        ref = pc.correct_compress(x64, h64, cfg.fs, cfg.fc, v[i], tec[t], lags=lags)
+        t_or += time.perf_counter() - t0
+        g = got[i, t].cpu().numpy()[lags]
+        errs.append(float(np.linalg.norm(g - ref) / np.linalg.norm(ref)))
+    ms_c = sum(res["compress"][0]) / steps
+    ms_p = sum(res["plain"][0]) / steps
+    ph_c = {k: round(vv[2] / steps, 4) for k, vv in res["compress"][1].items()}
+    ph_p = {k: round(vv[2] / steps, 4) for k, vv in res["plain"][1].items()}
+    line = {
+        "metric": METRIC, "value": n_samples / (ms_c / 1e3) / 1e6, "unit": UNIT, "n_gpus": 1,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms_c, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "doppler_bank_compressed", "n": cfg.n, "n_v": cfg.n_v, "n_tec": cfg.n_tec,
+                   "replica": f"LFM, {n_rep} samples, 5 MHz", "l2": L2_NOTE},
+        "latency_ms": {"p50": float(np.percentile(res["compress"][0], 50)),
+                       "p99": float(np.percentile(res["compress"][0], 99))},
+        "clocks": clk,
+        "plain_bank_ms_per_step": ms_p,
+        "added_cost_frac": (ms_c - ms_p) / ms_p,
+        "added_cost_frac_of_apply": (ms_c - ms_p) / ph_p.get("fused_apply", float("nan")),
+        "phases_ms_per_step": {"compress": ph_c, "plain": ph_p},
+        "error": {"rel_l2_max": max(errs), "pairs_checked": len(errs), "lags_per_pair": int(len(lags)),
+                  "tolerance": 1e-5},
+        "cpu_baseline": {"value": len(errs) * len(lags) / t_or / 1e6, "unit": "Mlags/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{len(errs)} (v_r, TEC) pairs x {len(lags)} lags (each a "
+                                   f"{n_rep}-term sum over the corrected buffer), {t_or:.1f} s"},
+    }
+    ctx.close()
+    return line
+
+
+def run_sub_workloads(args) -> dict:
+    """The other configurations, each in its own record with its clocks,
+    roofline or error and baselines (one GPU, after the bank)."""
+    import copy
+    import torch
+    subs = {}
+    plan = (("plain", run_plain, {}), ("batch", run_batch, {"steps": args.sub_steps}),
+            ("split", run_split, {"steps": args.sub_steps}),
+            ("serve", run_serve, {"serve_check_frac": min(args.serve_check_frac, 0.001)}),
+            ("compress_bank", run_compress, {}))
+    for name, fn, over in plan:
+        a = copy.copy(args)
+        a.n_v = None
+        for k, val in over.items():
+            setattr(a, k, val)
+        t0 = time.perf_counter()
+        try:
+            subs[name] = fn(a)
+        except Exception as e:                       # recorded, the headline still prints
+            subs[name] = {"error_running": f"{type(e).__name__}: {e}"}
+        subs[name]["bench_wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return subs
 
 
 def main() -> None:
@@ -905,10 +1045,15 @@ def main() -> None:
     ap.add_argument("--cpu-sample-v", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-v", type=int, default=None, help="fewer range rates (small profiling case)")
-    ap.add_argument("--workload", choices=["bank", "plain", "split", "batch", "serve"], default="bank",
-                    help="bank: the Doppler-bank headline line; plain: one LFM pulse, graph "
-                         "replays; split: the exact-sinc tensor-core GEMM; batch: the uneven "
-                         "batch; serve: the Poisson request stream")
+    ap.add_argument("--workload", choices=["all", "bank", "plain", "split", "batch", "serve", "compress"],
+                    default="all",
+                    help="all: the Doppler-bank headline line with every other workload as a "
+                         "sub-record (one GPU); bank: the headline alone; plain: one LFM pulse, "
+                         "graph replays; split: the exact-sinc tensor-core GEMM; batch: the "
+                         "uneven batch; serve: the Poisson request stream; compress: the bank "
+                         "with pulse compression")
+    ap.add_argument("--sub-steps", type=int, default=10,
+                    help="all: timed steps of the batch, split and compress sub-workloads")
     ap.add_argument("--replays", type=int, default=10000, help="plain: graph replays per mode")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="bank, batch: measure the schedule choices first (dc_autotune_*)")
@@ -933,19 +1078,20 @@ def main() -> None:
     if args.impl == "reference":
         run_reference(args, rank)
         return
-    if args.workload == "plain":
-        run_plain(args)
+    single = {"plain": run_plain, "split": run_split, "batch": run_batch, "serve": run_serve,
+              "compress": run_compress}
+    if args.workload in single:
+        if args.workload == "compress":
+            args.sub_steps = args.steps
+        elif args.workload in ("split", "batch") and args.steps > 50:
+            args.steps = 10
+        print(json.dumps(single[args.workload](args)), flush=True)
         return
-    if args.workload == "split":
-        run_split(args)
-        return
-    if args.workload == "batch":
-        run_batch(args)
-        return
-    if args.workload == "serve":
-        run_serve(args)
-        return
-    run_gpu(args, rank, world, local_rank)
+    line = run_gpu(args, rank, world, local_rank)
+    if args.workload == "all" and world == 1 and rank == 0:
+        line["workloads"] = run_sub_workloads(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

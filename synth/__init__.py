@@ -49,6 +49,22 @@ def bandlimited_noise(n: int, rng: np.random.Generator, frac: float = 0.8) -> np
     return x / np.sqrt(np.mean(np.abs(x) ** 2))
 
 
+def bandlimited_noise_batch(p: int, n: int, rng: np.random.Generator, frac: float = 0.8) -> np.ndarray:
+    """p pulses of band-limited noise at once, each by the recipe of
+    ``bandlimited_noise`` (rows of one (p, n) draw; complex128)."""
+    import os
+    import scipy.fft as sfft
+    w = np.empty((p, n), dtype=np.complex128)
+    w.real = rng.standard_normal((p, n))
+    w.imag = rng.standard_normal((p, n))
+    w *= 1.0 / np.sqrt(2.0)
+    W = sfft.fft(w, axis=-1, workers=os.cpu_count() or 1)
+    nu = np.fft.fftfreq(n)
+    W[:, np.abs(nu) > frac * 0.5] = 0.0
+    x = sfft.ifft(W, axis=-1, workers=os.cpu_count() or 1)
+    return x / np.sqrt(np.mean(np.abs(x) ** 2, axis=-1, keepdims=True))
+
+
 def tone(n: int, f_norm: float) -> np.ndarray:
     """exp(2 pi i f_norm m), f_norm in cycles/sample."""
     return np.exp(2j * np.pi * f_norm * np.arange(n, dtype=np.float64))
@@ -151,6 +167,16 @@ class SplitPrecisionBank:
         v = rng.uniform(-8000.0, 8000.0, self.n_alpha)
         p = self.n_pulses if n_pulses is None else n_pulses
         x = np.stack([bandlimited_noise(self.n, rng) for _ in range(p)])
+        return x, v
+
+    def draw_distinct(self):
+        """The stated workload: n_pulses distinct pulses per range rate.
+        Returns (x complex64 [n_alpha][n_pulses][n], v)."""
+        rng = rng_for(self.seed_index, salt=1)
+        v = rng.uniform(-8000.0, 8000.0, self.n_alpha)
+        x = np.empty((self.n_alpha, self.n_pulses, self.n), dtype=np.complex64)
+        for i in range(self.n_alpha):
+            x[i] = bandlimited_noise_batch(self.n_pulses, self.n, rng).astype(np.complex64)
         return x, v
 
 
