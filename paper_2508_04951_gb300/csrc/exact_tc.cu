@@ -224,16 +224,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int k8 = cbase + q;              // 16-byte chunk of the 64-byte row
         float v[8];
         const int m0 = kc * BK + k8 * 8;
+        // (m_n - m) + e_n with the integer part formed exactly first
+        // ((m_n - m0) - i, integers below 2^22) and e_n added last, so the
+        // denominator near m = m_n is e_n itself even when e_n is far below
+        // the rounding unit of m_n - m0
+        const float di0 = exact_i2f(mn - m0);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int m = m0 + i;
           float val = 0.f;
           if (m < a.n_in) {
-            // (m_n - m) + e_n: the integer part converted exactly, then e_n
-            // added once, so the denominator near m = m_n is e_n itself even
-            // when e_n is far below the rounding unit of the chunk's offset
             if (en == 0.f) val = (m == mn) ? 1.f : 0.f;
-            else val = __fdividef((i & 1) ? -sg : sg, exact_i2f(mn - m) + en);
+            else val = __fdividef((i & 1) ? -sg : sg, (di0 - (float)i) + en);
           }
           v[i] = val;
         }
