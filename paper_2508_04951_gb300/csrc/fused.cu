@@ -135,6 +135,59 @@ DC_DEV void row4096_1buf_arrive(float2 (&v)[16], float2* b, int j, const float2*
   dft16<DIR>(v);
 }
 
+// One 4096-point row with a single CTA barrier, thread j of 256.  In:
+// v[p] = x[256 p + j].  Out: v[b] = X[hw_sigma(j) + 256 b].
+// The four-step split 4096 = 16 x 256 (n = 256 p + q, k = s + 16 t):
+//   X[s + 16 t] = sum_q W256^(q t) [W4096^(q s) sum_p x[256 p + q] W16^(p s)]
+// -- thread q takes the length-16 DFT over p and the twiddle W4096^(q s);
+// one CTA-wide exchange gives half-warp s the 256 values of sub-problem s;
+// its length-256 DFT (256 = 16 x 16: q = 16 u + w, t = a + 16 b) takes a
+// length-16 DFT over u in thread w, the twiddle W256^(w a), a 16 x 16
+// transpose inside the half-warp (shared memory, __syncwarp only) and a
+// length-16 DFT over w in thread a.  Half-warp s only ever touches its own
+// 272-element region of b after the barrier, so the transpose needs no CTA
+// barrier.  ARRIVE: arrive at the cluster barrier (release) once this
+// thread's last read of b is done.  The caller must make sure nobody still
+// reads b when this starts; on return other threads may still read b.
+DC_DEV int hw_sigma(int j) { return (j >> 4) + ((j & 15) << 4); }
+
+// Where a received row keeps column c (c < COLS) of the column owner:
+// rpos(c) = 256 (c >> 8) + sw16(hw_sigma(c & 255)), sw16(x) = x ^ ((x >> 4)
+// & 15).  The half-warp row leaves column hw_sigma(j) + 256 m in thread j,
+// which so stores at 256 m + sw16(j): a warp's 32 remote stores fill one
+// 256-byte block (the XOR only permutes inside each 16-element group), the
+// form the distributed-shared-memory path moves fastest (scattered
+// addresses cost far more), while the owner's lanes, reading columns
+// 16 h + a (+ 256 p) at 16 a + (h ^ a), meet 16 different bank pairs.
+DC_DEV int sw16(int x) { return x ^ ((x >> 4) & 15); }
+DC_DEV int rpos(int c) { return (c & ~255) + sw16(hw_sigma(c & 255)); }
+
+template <int DIR, bool ARRIVE>
+DC_DEV void row4096_hw(float2 (&v)[16], float2* b, int j, const float2* __restrict__ tw) {
+  float2 w[4];
+  stage3_bases<DIR>(w, tw, j);                             // issued ahead of the DFT
+  dft16<DIR>(v);                                           // over p
+  apply_powers<16>(v, w);                                  // W4096^(q s), q = j
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b[pad16(256 * r + j)] = v[r];
+  const int s = j >> 4, t = j & 15;
+  stage2_bases<DIR>(w, tw, t);
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 16; ++u) v[u] = b[pad16(256 * s + 16 * u + t)];   // q = 16 u + w, w = t
+  dft16<DIR>(v);                                           // over u
+  apply_powers<16>(v, w);                                  // W256^(w a)
+  float2* reg = b + 272 * s;                               // = pad16(256 s): the half-warp's region
+  __syncwarp();                                            // its reads of the region are done
+#pragma unroll
+  for (int a = 0; a < 16; ++a) reg[17 * a + t] = v[a];     // V[w][a]
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = reg[17 * t + q];     // thread a = t: V[w = q][a]
+  if constexpr (ARRIVE) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  dft16<DIR>(v);                                           // over w
+}
+
 // The per-bin factors of the full correction on 16 bins k0 + s i held by one
 // thread: the caller's table (I.ptab, in the four-step layout, entries
 // t0 .. t0 + 15: exp(-i phi_k) times anything else the call bundles into the
@@ -262,10 +315,12 @@ template <int LOG2L1>
 __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
   constexpr int COLS = kRowN / L1;              // columns owned by a CTA
+  constexpr int PCOLS = COLS;                   // received rows at rpos(c)
   constexpr int PER = COLS / kRowThreads;       // columns per thread
   extern __shared__ __align__(128) float2 sm[];
   float2* A = sm;                               // [kRowPitch] row buffer, then
-  float2* R = sm;                               // [L1][COLS] received rows (L1 > 1)
+  float2* R = sm;                               // [L1][PCOLS] received rows (L1 > 1), column c
+                                                // of row q at q * PCOLS + rpos(c)
   __shared__ __align__(8) unsigned long long bar_in, bar_r;
 
   const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
@@ -292,7 +347,8 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
   for (int r = 0; r < 16; ++r) v[r] = cmul(A[j + 256 * r], v[r]);
   __syncthreads();                              // the row FFT overwrites A
   if constexpr (L1 == 1) row4096_1buf<+1>(v, A, j, a.tw);
-  else row4096_1buf_arrive<+1>(v, A, j, a.tw);  // arrives at the cluster barrier
+  else row4096_hw<+1, true>(v, A, j, a.tw);     // arrives at the cluster barrier; v[r] at
+                                                // n2 = hw_sigma(j) + 256 r
 
   if constexpr (L1 == 1) {
 #pragma unroll
@@ -304,12 +360,12 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
     // every peer's row FFT is done with its buffer and its bar_r is
     // initialised (the release arrive is inside the row FFT)
     cluster_wait<L1>();
-    const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
+    const uint32_t r_loc = smem_addr(R + k1 * PCOLS + sw16(j));    // rpos(hw_sigma(j))
     const uint32_t b_loc = smem_addr(&bar_r);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      const int owner = r / PER;                // n2 = j + 256 r -> owner n2 / COLS
-      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));
+      const int owner = r / PER;                // n2 = hw_sigma(j) + 256 r -> owner n2 / COLS
+      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));   // rpos(c + 256 m)
       st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
     }
     const float2* T = a.t4 + kT4Offset(L1);
@@ -323,7 +379,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
       if (p == 0) mbar_wait_cluster_bounded(&bar_r, 0, a.err);
       float2 col[L1];
 #pragma unroll
-      for (int q = 0; q < L1; ++q) col[q] = R[q * COLS + c];
+      for (int q = 0; q < L1; ++q) col[q] = R[q * PCOLS + rpos(c)];
       apply_powers<L1>(col, w);
       dft<L1, +1>(col);
 #pragma unroll
@@ -376,11 +432,12 @@ template <int LOG2L1>
 __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
   constexpr int COLS = kRowN / L1;              // columns owned by a CTA
+  constexpr int PCOLS = COLS;                   // received rows at rpos(c) (as in apply_kernel)
   constexpr int PER = COLS / kRowThreads;       // columns per thread
   constexpr int LOG2L = 12 + LOG2L1;
   extern __shared__ __align__(128) float2 sm[];
   float2* A = sm;                               // [kRowPitch] received row, row FFTs,
-  float2* R = sm;                               // then [L1][COLS] received inverse rows
+  float2* R = sm;                               // then [L1][PCOLS] received inverse rows
   __shared__ __align__(8) unsigned long long bar_r;
   const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const FftItem I = a.items[blockIdx.x >> LOG2L1];
@@ -460,20 +517,24 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
     __syncthreads();                            // the row FFT overwrites A
-    row4096_1buf<-1>(v, A, j, a.tw);
-    if (I.ph.enabled || I.ptab) {
-      // the forward row's last stage read A at exactly the addresses this
-      // thread writes first, so no barrier is needed before the regroup
+    row4096_hw<-1, false>(v, A, j, a.tw);      // v[r] = X[hw_sigma(j) + 256 r]
+    {
+      // back to natural order through A (the inverse row takes v[r] =
+      // Y[j + 256 r]), with the factors on runs of 16 bins on the way
+      const int sj = hw_sigma(j);
+      __syncthreads();                          // every half-warp is done with its region
 #pragma unroll
-      for (int r = 0; r < 16; ++r) A[pad16(j + 256 * r)] = v[r];
+      for (int r = 0; r < 16; ++r) A[pad16(sj + 256 * r)] = v[r];
       __syncthreads();
-      float2 u[16];
+      if (I.ph.enabled || I.ptab) {
+        float2 u[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
-      bin_factors(I, k1 + L1 * 16 * j, L1, k1 * kRowN + 16 * j, u);
+        for (int i = 0; i < 16; ++i) u[i] = A[pad16(16 * j + i)];
+        bin_factors(I, k1 + L1 * 16 * j, L1, k1 * kRowN + 16 * j, u);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
-      __syncthreads();
+        for (int i = 0; i < 16; ++i) A[pad16(16 * j + i)] = u[i];
+        __syncthreads();
+      }
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
     }
@@ -483,13 +544,13 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
     __syncthreads();                            // the inverse row writes A first
     // phase 1 of bar_r: the inverse rows (phase 0 has completed above)
     if (j == 0) mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
-    row4096_1buf_arrive<+1>(v, A, j, a.tw);     // arrives at the cluster barrier
+    row4096_hw<+1, true>(v, A, j, a.tw);        // arrives at the cluster barrier
     cluster_wait<L1>();                         // every peer's buffer is free, bar_r re-armed
-    const uint32_t r_loc = smem_addr(R + k1 * COLS + j);
+    const uint32_t r_loc = smem_addr(R + k1 * PCOLS + sw16(j));    // rpos(hw_sigma(j))
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      const int owner = r / PER;                // n2 = j + 256 r -> owner n2 / COLS
-      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));
+      const int owner = r / PER;                // n2 = hw_sigma(j) + 256 r -> owner n2 / COLS
+      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));   // rpos(c + 256 m)
       st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
     }
 #pragma unroll
@@ -502,7 +563,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
       if (p == 0) mbar_wait_cluster_bounded(&bar_r, 1, a.err);
       float2 col[L1];
 #pragma unroll
-      for (int q = 0; q < L1; ++q) col[q] = R[q * COLS + c];
+      for (int q = 0; q < L1; ++q) col[q] = R[q * PCOLS + rpos(c)];
       apply_powers<L1>(col, w);
       dft<L1, +1>(col);
 #pragma unroll
@@ -559,21 +620,24 @@ __global__ void __launch_bounds__(kRowThreads, 4) row_mid_kernel(RowArgs a) {
   float2 v[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = src[j + 256 * r];
-  row4096_1buf<-1>(v, bufA, j, a.tw);
-  if (I.ph.enabled || I.ptab) {
-    // factor of bin k = k1 + L1 k2, each thread on 16 consecutive k2 (the
-    // forward row's last stage read A at exactly the addresses this thread
-    // writes now, so no barrier is needed first)
+  row4096_hw<-1, false>(v, bufA, j, a.tw);    // v[r] = X[hw_sigma(j) + 256 r]
+  {
+    // back to natural order through A, with the factor of bin k = k1 + L1 k2
+    // on the way (each thread on 16 consecutive k2)
+    const int sj = hw_sigma(j);
+    __syncthreads();                           // every half-warp is done with its region
 #pragma unroll
-    for (int r = 0; r < 16; ++r) bufA[pad16(j + 256 * r)] = v[r];
+    for (int r = 0; r < 16; ++r) bufA[pad16(sj + 256 * r)] = v[r];
     __syncthreads();
-    float2 u[16];
+    if (I.ph.enabled || I.ptab) {
+      float2 u[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) u[i] = bufA[pad16(16 * j + i)];
-    bin_factors(I, k1 + L1 * 16 * j, L1, k1 * kRowN + 16 * j, u);
+      for (int i = 0; i < 16; ++i) u[i] = bufA[pad16(16 * j + i)];
+      bin_factors(I, k1 + L1 * 16 * j, L1, k1 * kRowN + 16 * j, u);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) bufA[pad16(16 * j + i)] = u[i];
-    __syncthreads();
+      for (int i = 0; i < 16; ++i) bufA[pad16(16 * j + i)] = u[i];
+      __syncthreads();
+    }
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = bufA[pad16(j + 256 * r)];
   }
