@@ -84,8 +84,9 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 100):
         self.index = index
+        self.period_ms = int(period_ms)
         self.proc = None
         self.path = None
 
@@ -95,7 +96,8 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+                 "-lms", str(self.period_ms), "-f", self.path], stdout=subprocess.DEVNULL,
+                stderr=subprocess.DEVNULL)
             # the sampler must not outlive the run, whatever way it ends (a
             # profiler waits for every process the run started)
             atexit.register(self._end)
@@ -837,8 +839,11 @@ def run_serve(args) -> dict:
         kept[i] = np.empty(int(lens[i]), dtype=np.complex64)
         kept[i].fill(0)
     th = threading.Thread(target=submitter)
-    clocks = Clocks(0)
-    clocks.start()
+    # clocks sampled once a second here: each query takes the driver for a
+    # moment, and at 10 queries a second that shows in the latency tail
+    clocks = Clocks(0, period_ms=args.serve_clock_ms)
+    if args.serve_clock_ms > 0:
+        clocks.start()
     t_start = time.perf_counter()
     th.start()
     for i in range(nreq):
@@ -1068,6 +1073,8 @@ def main() -> None:
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--serial-seconds", type=float, default=1.0, help="serve: seconds for the serial server")
     ap.add_argument("--slots", type=int, default=3, help="serve: batches in flight")
+    ap.add_argument("--serve-clock-ms", type=int, default=1000,
+                    help="serve: clock sampling period during the stream (0: none)")
     ap.add_argument("--split-mode", choices=["bf16x3", "fp16x3"], default="bf16x3")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -268,9 +268,9 @@ double kaiser_fp64(double u, double R, double beta) {
 // Per-tap polynomial of the window in the fractional delay e in [0, 1]:
 // w(e - k) = sum_d c[d] e^d, degree kWCoef-1, interpolating at Chebyshev
 // nodes of [0, 1] (solved in FP64).  Layout [tap t = k + R - 1][kWCoef].
-std::vector<float> window_poly(int taps, double beta) {
+std::vector<double> window_poly_fit(int taps, double beta) {
   const int R = taps / 2, D = kWCoef;
-  std::vector<float> out((size_t)taps * D);
+  std::vector<double> out((size_t)taps * D);
   const double pi = 3.14159265358979323846;
   double nodes[kWCoef];
   for (int i = 0; i < D; ++i) nodes[i] = 0.5 + 0.5 * std::cos(pi * (i + 0.5) / D);
@@ -298,7 +298,28 @@ std::vector<float> window_poly(int taps, double beta) {
       for (int d = c + 1; d < D; ++d) v -= A[c][d] * coef[d];
       coef[c] = v / A[c][c];
     }
-    for (int d = 0; d < D; ++d) out[(size_t)t * D + d] = (float)coef[d];
+    for (int d = 0; d < D; ++d) out[(size_t)t * D + d] = coef[d];
+  }
+  return out;
+}
+
+std::vector<float> window_poly(int taps, double beta) {
+  const std::vector<double> c = window_poly_fit(taps, beta);
+  return std::vector<float>(c.begin(), c.end());
+}
+
+// The same polynomials and their first two derivatives in e, per tap
+// [w (8 coefficients) | w' (7, then 0) | w'' (6, then 0, 0)].
+std::vector<float> window_poly_d012(int taps, double beta) {
+  const std::vector<double> c = window_poly_fit(taps, beta);
+  const int D = kWCoef;
+  std::vector<float> out((size_t)taps * 3 * D, 0.f);
+  for (int t = 0; t < taps; ++t) {
+    const double* ct = &c[(size_t)t * D];
+    float* o = &out[(size_t)t * 3 * D];
+    for (int d = 0; d < D; ++d) o[d] = (float)ct[d];
+    for (int d = 0; d + 1 < D; ++d) o[D + d] = (float)((d + 1) * ct[d + 1]);
+    for (int d = 0; d + 2 < D; ++d) o[2 * D + d] = (float)((d + 2) * (d + 1) * ct[d + 2]);
   }
   return out;
 }
@@ -438,7 +459,7 @@ dc_status run_resample_tc(dc_ctx* c, const float2* x, int n_in, int n_out, const
     const double spread = (dl[order[last]] - dl[order[g]]) * ((double)n_out + 64.0) + 2.0;
     if (spread > (double)rs_tc_max_span()) return DC_EINVAL;
   }
-  const std::vector<float> wp = window_poly(o.taps, o.kaiser_beta);
+  const std::vector<float> wp = window_poly_d012(o.taps, o.kaiser_beta);
   std::vector<float> dls(2 * (size_t)n_v);
   std::vector<int> vidx(n_v);
   for (int i = 0; i < n_v; ++i) {

@@ -78,7 +78,8 @@ struct RsTcArgs {
   const float* dl;
   const int* vidx;
   int n_slots;
-  const float* wpoly;  // 32-tap window polynomials, as RsArgs::wpoly
+  const float* wpoly;  // 32-tap window polynomials and their first two
+                       // derivatives: [tap][3][kWCoef] (w, w', w'' in e)
   int* err;
 };
 int rs_tc_max_span();

@@ -83,22 +83,15 @@ DC_DEV void sinc_d012(float a, float S, float C, float& s0, float& s1, float& s2
 }
 
 // Window w(e - j) and its first two derivatives in e from tap t's degree-7
-// polynomial (t = j + 15).
-DC_DEV void window_d012(const float* __restrict__ wp, int t, float e, float& w0, float& w1,
-                        float& w2) {
-  const float4 lo = __ldg(reinterpret_cast<const float4*>(wp + t * kWCoef));
-  const float4 hi = __ldg(reinterpret_cast<const float4*>(wp + t * kWCoef + 4));
-  const float c[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-  float p0 = c[7], p1 = 7.f * c[7], p2 = 42.f * c[7];
-#pragma unroll
-  for (int d = 6; d >= 0; --d) {
-    p0 = fmaf(p0, e, c[d]);
-    if (d >= 1) p1 = fmaf(p1, e, (float)d * c[d]);
-    if (d >= 2) p2 = fmaf(p2, e, (float)(d * (d - 1)) * c[d]);
-  }
-  w0 = p0;
-  w1 = p1;
-  w2 = p2;
+// polynomial and its derivative polynomials (t = j + 15), staged in shared
+// memory as [tap][3][8] coefficients.
+DC_DEV void window_d012(const float* wp, int t, float e, float& w0, float& w1, float& w2) {
+  const float4* q = reinterpret_cast<const float4*>(wp + t * 3 * kWCoef);
+  const float4 a0 = q[0], a1 = q[1], b0 = q[2], b1 = q[3], c0 = q[4], c1 = q[5];
+  w0 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(a1.w, e, a1.z), e, a1.y), e, a1.x), e, a0.w), e, a0.z), e, a0.y),
+            e, a0.x);
+  w1 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(b1.z, e, b1.y), e, b1.x), e, b0.w), e, b0.z), e, b0.y), e, b0.x);
+  w2 = fmaf(fmaf(fmaf(fmaf(fmaf(c1.y, e, c1.x), e, c0.w), e, c0.z), e, c0.y), e, c0.x);
 }
 
 DC_DEV uint32_t pack_half2(float a, float b) {
@@ -122,6 +115,7 @@ DC_DEV void split8_f16(const float (&v)[8], uint4& hi, uint4& lo) {
 __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ float2 win[kWin];
+  __shared__ __align__(16) float s_wp[32 * 3 * kWCoef];
   __shared__ int s_m[kV], s_vidx[kV];
   __shared__ float s_e[kV], s_sin[kV], s_cos[kV], s_dl[kV];
   __shared__ float s_max[kThreads / 32];
@@ -138,6 +132,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
   const int g0 = blockIdx.y * kV;
   const float nc = (float)n0 + 0.5f * (kTile - 1);          // tile centre (half-integer, exact)
 
+  for (int i = threadIdx.x; i < 32 * 3 * kWCoef; i += kThreads) s_wp[i] = __ldg(a.wpoly + i);
   // 1. per range rate: delta_v n_c = m_v + e_v, and the K range of the tile
   if (warp == 0) {
     const int slot = g0 + lane;
@@ -249,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
           const float sg = (j & 1) ? -1.f : 1.f;
           float s0, s1, s2, w0, w1, w2;
           sinc_d012(e - (float)j, sg * sn, sg * cs, s0, s1, s2);
-          window_d012(a.wpoly, j + 15, e, w0, w1, w2);
+          window_d012(s_wp, j + 15, e, w0, w1, w2);
           h0 = s0 * w0;
           h1 = fmaf(s1, w0, s0 * w1);
           h2 = fmaf(s2, w0, fmaf(2.f * s1, w1, s0 * w2));
