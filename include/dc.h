@@ -429,6 +429,16 @@ DC_API dc_status dc_autotune_bank(dc_ctx* ctx, const dc_c64* x_dev, long long n,
 DC_API dc_status dc_tuning_get(const dc_ctx* ctx, dc_tuning* out);
 DC_API dc_status dc_tuning_set(dc_ctx* ctx, const dc_tuning* t);
 
+/* Schedule cache: dc_tuning_save writes the context's schedule to `path` as
+ * a small JSON object ({"format": "dc_tuning/1", "resample_q": .., "resample_tc":
+ * .., "fft": {"<m>": ..}, "chunk": {"<m>": ..}}); dc_tuning_load reads such a
+ * file and applies it as dc_tuning_set would (DC_EINVAL for a missing or
+ * malformed file or an invalid schedule).  With the environment variable
+ * DC_TUNING_CACHE naming a file, dc_create loads it when it exists and every
+ * dc_autotune_* call writes its result there. */
+DC_API dc_status dc_tuning_save(const dc_ctx* ctx, const char* path);
+DC_API dc_status dc_tuning_load(dc_ctx* ctx, const char* path);
+
 #ifdef __cplusplus
 }
 #endif

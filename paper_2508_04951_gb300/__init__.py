@@ -136,6 +136,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                  ctypes.POINTER(DcTuning)]),
         "dc_tuning_get": (i, [vp, ctypes.POINTER(DcTuning)]),
         "dc_tuning_set": (i, [vp, ctypes.POINTER(DcTuning)]),
+        "dc_tuning_save": (i, [vp, ctypes.c_char_p]),
+        "dc_tuning_load": (i, [vp, ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -576,3 +578,15 @@ def dc_tuning_set(ctx: Context, schedule: dict | None) -> None:
         t.chunk[int(m)] = int(v)
     ctx.check(ctx.lib.dc_tuning_set(ctx.handle, ctypes.byref(t)))
 
+
+
+def dc_tuning_save(ctx: Context, path: str) -> None:
+    """Write the context's schedule to a JSON file (dc_tuning/1)."""
+    st = ctx.lib.dc_tuning_save(ctx.handle, os.fsencode(path))
+    if st:
+        raise DcError(st, f"could not write {path}")
+
+
+def dc_tuning_load(ctx: Context, path: str) -> None:
+    """Apply a schedule written by dc_tuning_save."""
+    ctx.check(ctx.lib.dc_tuning_load(ctx.handle, os.fsencode(path)))

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -655,6 +656,14 @@ dc_status dc_create(dc_ctx** out, int device, size_t budget) {
     if (c->err) cudaFree(c->err);
     delete c;
     return DC_ENOMEM;
+  }
+  // a schedule cache named by DC_TUNING_CACHE is loaded when it exists (a
+  // missing or unreadable file leaves the built-in rules)
+  if (const char* path = getenv("DC_TUNING_CACHE")) {
+    if (FILE* f = fopen(path, "r")) {
+      fclose(f);
+      if (dc_tuning_load(c, path) != DC_OK) c->tune = dc_ctx::Tune{};
+    }
   }
   *out = c;
   return DC_OK;
@@ -1576,6 +1585,7 @@ dc_status autotune(dc_ctx* c, F&& call, std::vector<Choice> choices, cudaStream_
   if (!st) st = call();                        // outputs from the chosen schedule
   if (!st && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(c, e, "tuned run");
   if (st) return st;
+  if (const char* path = getenv("DC_TUNING_CACHE")) dc_tuning_save(c, path);
   if (report) {
     tuning_out(c, report);
     report->ms_default = ms_default;
@@ -1705,4 +1715,131 @@ dc_status dc_internal_correct_batch_ws(dc_ctx* c, const dc_c64* in, dc_c64* out,
   c->ws = ws0;
   c->ws_bytes = b0;
   return st;
+}
+
+// ------------------------------------------------------ schedule cache
+// The context's schedule as a small JSON object, e.g.
+//   {"format": "dc_tuning/1", "resample_q": 0, "resample_tc": 1,
+//    "fft": {"16": 1}, "chunk": {"17": 67108864}}
+// (only non-zero entries of fft / chunk are written).
+namespace {
+
+std::string tuning_json(const dc_ctx* c) {
+  std::string s = "{\"format\": \"dc_tuning/1\", \"resample_q\": " + std::to_string(c->tune.rs_q) +
+                  ", \"resample_tc\": " + std::to_string(c->tune.rs_tc) + ", \"fft\": {";
+  bool first = true;
+  for (int m = 0; m <= 20; ++m)
+    if (c->tune.fft[m]) {
+      s += (first ? "\"" : ", \"") + std::to_string(m) + "\": " + std::to_string(c->tune.fft[m]);
+      first = false;
+    }
+  s += "}, \"chunk\": {";
+  first = true;
+  for (int m = 0; m <= 20; ++m)
+    if (c->tune.chunk[m]) {
+      s += (first ? "\"" : ", \"") + std::to_string(m) + "\": " + std::to_string(c->tune.chunk[m]);
+      first = false;
+    }
+  return s + "}}\n";
+}
+
+// Minimal reader for the object tuning_json writes: a flat key -> integer map
+// and two nested maps of decimal keys.  Returns false on anything else.
+struct JsonIn {
+  const char* p;
+  void ws() { while (*p == ' ' || *p == '\n' || *p == '\r' || *p == '\t') ++p; }
+  bool lit(char ch) { ws(); if (*p != ch) return false; ++p; return true; }
+  bool str(std::string& out) {
+    ws();
+    if (*p != '"') return false;
+    const char* e = strchr(p + 1, '"');
+    if (!e) return false;
+    out.assign(p + 1, e);
+    p = e + 1;
+    return true;
+  }
+  bool num(long long& v) {
+    ws();
+    char* e = nullptr;
+    v = strtoll(p, &e, 10);
+    if (e == p) return false;
+    p = e;
+    return true;
+  }
+};
+
+bool parse_map(JsonIn& in, long long (&out)[21]) {
+  if (!in.lit('{')) return false;
+  in.ws();
+  if (*in.p == '}') { ++in.p; return true; }
+  while (true) {
+    std::string k;
+    long long v;
+    if (!in.str(k) || !in.lit(':') || !in.num(v)) return false;
+    char* e = nullptr;
+    const long m = strtol(k.c_str(), &e, 10);
+    if (!e || *e || m < 0 || m > 20) return false;
+    out[m] = v;
+    if (in.lit(',')) continue;
+    return in.lit('}');
+  }
+}
+
+bool parse_tuning(const std::string& text, dc_tuning& t) {
+  t = dc_tuning{};
+  long long fft[21] = {}, chunk[21] = {};
+  JsonIn in{text.c_str()};
+  if (!in.lit('{')) return false;
+  bool format_ok = false;
+  while (true) {
+    std::string k;
+    if (!in.str(k) || !in.lit(':')) return false;
+    if (k == "format") {
+      std::string f;
+      if (!in.str(f)) return false;
+      format_ok = f == "dc_tuning/1";
+    } else if (k == "resample_q" || k == "resample_tc") {
+      long long v;
+      if (!in.num(v)) return false;
+      (k == "resample_q" ? t.resample_q : t.resample_tc) = (int)v;
+    } else if (k == "fft" || k == "chunk") {
+      if (!parse_map(in, k == "fft" ? fft : chunk)) return false;
+    } else {
+      return false;
+    }
+    if (in.lit(',')) continue;
+    if (!in.lit('}')) return false;
+    break;
+  }
+  for (int m = 0; m <= 20; ++m) {
+    t.fft[m] = (int)fft[m];
+    t.chunk[m] = chunk[m];
+  }
+  return format_ok;
+}
+
+}  // namespace
+
+extern "C" dc_status dc_tuning_save(const dc_ctx* c, const char* path) {
+  if (!c || !path) return DC_EINVAL;
+  const std::string s = tuning_json(c);
+  FILE* f = fopen(path, "w");
+  if (!f) return DC_EINVAL;
+  const bool ok = fwrite(s.data(), 1, s.size(), f) == s.size();
+  return (fclose(f) == 0 && ok) ? DC_OK : DC_EINVAL;
+}
+
+extern "C" dc_status dc_tuning_load(dc_ctx* c, const char* path) {
+  if (!c || !path) return DC_EINVAL;
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(c, DC_EINVAL, "cannot open schedule file %s", path);
+  std::string text;
+  char buf[4096];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0 && text.size() < (1u << 20)) text.append(buf, k);
+  fclose(f);
+  dc_tuning t;
+  if (!parse_tuning(text, t)) return fail(c, DC_EINVAL, "%s is not a dc_tuning/1 schedule", path);
+  return dc_tuning_set(c, &t);
 }

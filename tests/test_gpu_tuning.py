@@ -136,3 +136,32 @@ def test_tuning_set_rejects_bad_schedules(dcg, ctx):
         with pytest.raises(dcg.DcError):
             dcg.dc_tuning_set(ctx, bad)
     assert dcg.dc_tuning_get(ctx)["fft"] == {}
+
+
+def test_schedule_cache_round_trip(dcg, ctx, tmp_path, monkeypatch):
+    sched = {"resample_q": 4, "resample_tc": 2, "fft": {13: 2, 16: 1}, "chunk": {17: 64 << 20}}
+    dcg.dc_tuning_set(ctx, sched)
+    path = str(tmp_path / "sched.json")
+    dcg.dc_tuning_save(ctx, path)
+    text = open(path).read()
+    assert '"format": "dc_tuning/1"' in text
+    other = dcg.Context(0)
+    dcg.dc_tuning_load(other, path)
+    got = dcg.dc_tuning_get(other)
+    assert (got["resample_q"], got["resample_tc"], got["fft"], got["chunk"]) == \
+        (4, 2, {13: 2, 16: 1}, {17: 64 << 20})
+    other.close()
+    # a context created with DC_TUNING_CACHE set starts from that file
+    monkeypatch.setenv("DC_TUNING_CACHE", path)
+    third = dcg.Context(0)
+    assert dcg.dc_tuning_get(third)["fft"] == {13: 2, 16: 1}
+    third.close()
+    monkeypatch.delenv("DC_TUNING_CACHE")
+    # malformed files and invalid schedules are refused and change nothing
+    bad = tmp_path / "bad.json"
+    for body in ('{"format": "dc_tuning/1", "fft": {"3": 2}}', "not json", '{"format": "other"}'):
+        bad.write_text(body)
+        with pytest.raises(dcg.DcError):
+            dcg.dc_tuning_load(ctx, str(bad))
+    assert dcg.dc_tuning_get(ctx)["resample_q"] == 4
+    dcg.dc_tuning_set(ctx, None)
