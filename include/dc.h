@@ -397,9 +397,12 @@ DC_API dc_status dc_serve_counters(dc_server* server, dc_serve_info* out);
  *   resample_tc the bank's windowed resampling: 1 = tensor cores (a GEMM of
  *               the pulse's Hankel tiles with per-range-rate tap weights and
  *               their derivatives, fp16 hi/lo operands; used where the range
- *               rates allow it), 2 = the CUDA-core kernel.
+ *               rates allow it), 2 = the CUDA-core kernel;
+ *   apply_rows  the cluster-fused spectrum apply (bank, L >= 32768): 1 = one
+ *               4096-point row per CTA (clusters of L / 4096 CTAs), 2 = two
+ *               rows per CTA (clusters of half that size).
  * 0 in any field means the library's built-in rule (tensor cores where
- * eligible for resample_tc). */
+ * eligible for resample_tc, one row per CTA for apply_rows). */
 typedef struct {
   int resample_q;
   int fft[21];
@@ -408,6 +411,7 @@ typedef struct {
   double ms_best;       /* the same call under the chosen schedule              */
   int candidates;       /* schedules timed                                      */
   int resample_tc;
+  int apply_rows;
 } dc_tuning;
 
 /* Measure the schedule choices the call meets on its own data (each
@@ -431,7 +435,7 @@ DC_API dc_status dc_tuning_set(dc_ctx* ctx, const dc_tuning* t);
 
 /* Schedule cache: dc_tuning_save writes the context's schedule to `path` as
  * a small JSON object ({"format": "dc_tuning/1", "resample_q": .., "resample_tc":
- * .., "fft": {"<m>": ..}, "chunk": {"<m>": ..}}); dc_tuning_load reads such a
+ * .., "apply_rows": .., "fft": {"<m>": ..}, "chunk": {"<m>": ..}}); dc_tuning_load reads such a
  * file and applies it as dc_tuning_set would (DC_EINVAL for a missing or
  * malformed file or an invalid schedule).  With the environment variable
  * DC_TUNING_CACHE naming a file, dc_create loads it when it exists and every

@@ -70,6 +70,7 @@ struct dc_ctx {
     long long chunk[21] = {};  // three-pass intermediate bytes per chunk (-1: whole class)
     int fft[21] = {};          // 4096 <= L <= 65536: 1 cluster-fused, 2 three passes
     int rs_tc = 0;             // bank resampling: 1 tensor cores (where eligible), 2 CUDA cores
+    int apply_rows = 0;        // spectrum apply at L >= 32768: rows per CTA, 1 or 2
   } tune;
   std::recursive_mutex mu;
 };
@@ -105,6 +106,10 @@ bool fused_L(int log2L) { return log2L >= 12 && log2L <= 16; }
 // 65536 unless tuned otherwise), else one row pass (L <= 4096) or three
 // passes over an intermediate processed in chunks.
 bool use_fused(const dc_ctx* c, int log2L) { return fused_L(log2L) && c->tune.fft[log2L] != 2; }
+// Two rows per CTA in the spectrum-apply kernel (L >= 32768 only).  The
+// built-in rule keeps one: on the 256 x 16 bank at L = 65536 two rows (8-CTA
+// clusters, 2 CTAs per SM) ran 1.46 ms against 1.36 ms.
+bool apply_rows2(const dc_ctx* c, int log2L) { return log2L >= 15 && c->tune.apply_rows == 2; }
 
 // Transforms per chunk of a three-pass class.  The tuned intermediate size
 // wins; else `dflt` bytes (0: the whole class at once -- the batch, whose
@@ -1129,6 +1134,7 @@ dc_status bank_impl(dc_ctx* c, const dc_c64* x, long long n, const dc_c64* rep, 
   if (fused) {
     if ((st = upload(c, ap, item_at, s, &dev))) return st;
     FusedArgs a{dev, (int)n_pairs, log2L, c->tw, c->err, c->t4};
+    a.apply_rows2 = apply_rows2(c, log2L);
     Phase ph(c, PH_FUSED_APPLY, s, (long long)n_pairs * n_out);
     if ((e = launch_fused(FUSED_APPLY, a, s)) != cudaSuccess) return cuda_fail(c, e, "apply launch");
     return DC_OK;
@@ -1498,19 +1504,21 @@ extern "C" dc_status dc_plan_destroy(dc_plan* p) {
 namespace {
 
 struct Choice {
-  int kind;   // 0 resample_q, 1 fft[m], 2 chunk[m], 3 bank resampling engine
+  int kind;   // 0 resample_q, 1 fft[m], 2 chunk[m], 3 bank resampling engine, 4 apply rows per CTA
   int m;
   std::vector<long long> values;
 };
 
 long long tune_get(const dc_ctx* c, const Choice& d) {
+  if (d.kind == 4) return c->tune.apply_rows;
   if (d.kind == 3) return c->tune.rs_tc;
   if (d.kind == 0) return c->tune.rs_q;
   if (d.kind == 1) return c->tune.fft[d.m];
   return c->tune.chunk[d.m];
 }
 void tune_set(dc_ctx* c, const Choice& d, long long v) {
-  if (d.kind == 3) c->tune.rs_tc = (int)v;
+  if (d.kind == 4) c->tune.apply_rows = (int)v;
+  else if (d.kind == 3) c->tune.rs_tc = (int)v;
   else if (d.kind == 0) c->tune.rs_q = (int)v;
   else if (d.kind == 1) c->tune.fft[d.m] = (int)v;
   else c->tune.chunk[d.m] = v;
@@ -1543,6 +1551,7 @@ void tuning_out(const dc_ctx* c, dc_tuning* t) {
   *t = dc_tuning{};
   t->resample_q = c->tune.rs_q;
   t->resample_tc = c->tune.rs_tc;
+  t->apply_rows = c->tune.apply_rows;
   for (int m = 0; m <= 20; ++m) {
     t->fft[m] = c->tune.fft[m];
     t->chunk[m] = c->tune.chunk[m];
@@ -1655,6 +1664,7 @@ extern "C" dc_status dc_autotune_bank(dc_ctx* c, const dc_c64* x, long long n, c
   if (o.mode == DC_WINDOWED && o.taps == 32 && !o.carrier_shift) ch.push_back({3, 0, {1, 2}});
   if (o.mode == DC_WINDOWED && o.taps == 32 && q8) ch.push_back({0, 0, {8, 4}});
   class_choices(ch, log2_ceil(n_out), (size_t)n_v * n_tec);
+  if (log2_ceil(n_out) >= 15 && log2_ceil(n_out) <= 16) ch.push_back({4, 0, {2, 1}});
   cudaSetDevice(c->device);
   cudaStream_t s = S(stream);
   return autotune(
@@ -1679,6 +1689,8 @@ extern "C" dc_status dc_tuning_set(dc_ctx* c, const dc_tuning* t) {
     return fail(c, DC_EINVAL, "resample_q must be 0, 4 or 8");
   if (t->resample_tc < 0 || t->resample_tc > 2)
     return fail(c, DC_EINVAL, "resample_tc must be 0, 1 or 2");
+  if (t->apply_rows < 0 || t->apply_rows > 2)
+    return fail(c, DC_EINVAL, "apply_rows must be 0, 1 or 2");
   for (int m = 0; m <= 20; ++m) {
     if (t->fft[m] < 0 || t->fft[m] > 2 || (t->fft[m] && (m < 12 || m > 16)))
       return fail(c, DC_EINVAL, "fft[%d] must be 0, 1 or 2 (and 0 outside 4096 <= L <= 65536)", m);
@@ -1686,6 +1698,7 @@ extern "C" dc_status dc_tuning_set(dc_ctx* c, const dc_tuning* t) {
   }
   c->tune.rs_q = t->resample_q;
   c->tune.rs_tc = t->resample_tc;
+  c->tune.apply_rows = t->apply_rows;
   for (int m = 0; m <= 20; ++m) {
     c->tune.fft[m] = t->fft[m];
     c->tune.chunk[m] = t->chunk[m];
@@ -1720,13 +1733,14 @@ dc_status dc_internal_correct_batch_ws(dc_ctx* c, const dc_c64* in, dc_c64* out,
 // ------------------------------------------------------ schedule cache
 // The context's schedule as a small JSON object, e.g.
 //   {"format": "dc_tuning/1", "resample_q": 0, "resample_tc": 1,
-//    "fft": {"16": 1}, "chunk": {"17": 67108864}}
+//    "apply_rows": 0, "fft": {"16": 1}, "chunk": {"17": 67108864}}
 // (only non-zero entries of fft / chunk are written).
 namespace {
 
 std::string tuning_json(const dc_ctx* c) {
   std::string s = "{\"format\": \"dc_tuning/1\", \"resample_q\": " + std::to_string(c->tune.rs_q) +
-                  ", \"resample_tc\": " + std::to_string(c->tune.rs_tc) + ", \"fft\": {";
+                  ", \"resample_tc\": " + std::to_string(c->tune.rs_tc) +
+                  ", \"apply_rows\": " + std::to_string(c->tune.apply_rows) + ", \"fft\": {";
   bool first = true;
   for (int m = 0; m <= 20; ++m)
     if (c->tune.fft[m]) {
@@ -1798,10 +1812,10 @@ bool parse_tuning(const std::string& text, dc_tuning& t) {
       std::string f;
       if (!in.str(f)) return false;
       format_ok = f == "dc_tuning/1";
-    } else if (k == "resample_q" || k == "resample_tc") {
+    } else if (k == "resample_q" || k == "resample_tc" || k == "apply_rows") {
       long long v;
       if (!in.num(v)) return false;
-      (k == "resample_q" ? t.resample_q : t.resample_tc) = (int)v;
+      (k == "resample_q" ? t.resample_q : k == "resample_tc" ? t.resample_tc : t.apply_rows) = (int)v;
     } else if (k == "fft" || k == "chunk") {
       if (!parse_map(in, k == "fft" ? fft : chunk)) return false;
     } else {

@@ -215,9 +215,10 @@ template <int CL> DC_DEV void cluster_wait() {
 // Spectra (FUSED_SPEC): one row k1 of the four-step spectrum per CTA, one
 // cluster of L1 CTAs per transform.  Each CTA runs the length-L1 forward
 // DFTs of its 4096 / L1 columns straight from global memory, applies
-// W_L^(n2 k1) and sends element k1 of column n2 to the CTA owning row k1
-// (asynchronous remote stores counted on that CTA's receive mbarrier, so no
-// release fence); the received row is transformed in the same buffer.
+// W_L^(n2 k1) and writes element k1 of column n2 into the shared memory of
+// the CTA owning row k1 (plain remote stores between two cluster barriers:
+// every peer running before, every column delivered after); the received
+// row is transformed in the same buffer.
 template <int LOG2L1>
 __global__ void __launch_bounds__(kRowThreads, 4) spec_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
@@ -225,7 +226,6 @@ __global__ void __launch_bounds__(kRowThreads, 4) spec_kernel(FusedArgs a) {
   constexpr int PER = COLS / kRowThreads;       // columns per thread
   extern __shared__ __align__(128) float2 sm[];
   float2* A = sm;                               // [kRowPitch] received row, row FFT buffer
-  __shared__ __align__(8) unsigned long long bar_r;
   const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const FftItem I = a.items[blockIdx.x >> LOG2L1];
   const int j = threadIdx.x;
@@ -237,14 +237,8 @@ __global__ void __launch_bounds__(kRowThreads, 4) spec_kernel(FusedArgs a) {
       v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
     }
   } else {
-    if (j == 0) {
-      mbar_init(&bar_r, 1);
-      mbar_expect_tx(&bar_r, kRowN * sizeof(float2));
-    }
-    __syncthreads();
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");   // bar_r published
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");   // this CTA runs
     const float2* T = a.t4 + kT4Offset(L1);
-    const uint32_t b_loc = smem_addr(&bar_r);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int n2 = k1 * COLS + j + 256 * p;
@@ -259,12 +253,13 @@ __global__ void __launch_bounds__(kRowThreads, 4) spec_kernel(FusedArgs a) {
 #pragma unroll
       for (int b = 0; b < LOG2L1; ++b) w[b] = conj_if<+1>(__ldg(T + b * kRowN + n2));
       apply_powers<L1>(col, w);
-      if (p == 0) cluster_wait<L1>();           // every receive barrier is initialised
+      if (p == 0) cluster_wait<L1>();           // every peer runs: its shared memory exists
       const uint32_t dst = smem_addr(A + pad16(n2));
 #pragma unroll
-      for (int q = 0; q < L1; ++q) st_async_c64(dsmem_map(dst, q), col[q], dsmem_map(b_loc, q));
+      for (int q = 0; q < L1; ++q) st_cluster_c64(dsmem_map(dst, q), col[q]);
     }
-    mbar_wait_cluster_bounded(&bar_r, 0, a.err);
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");   // columns delivered
+    cluster_wait<L1>();
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
     __syncthreads();                            // the row FFT overwrites A
@@ -301,54 +296,60 @@ cudaError_t launch_spec(const FusedArgs& a, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-// Spectrum apply (FUSED_APPLY): one row k1 of the transform per CTA, one
-// cluster of L1 CTAs per transform.  The spectrum row arrives by one 32 KiB
-// bulk copy, the phase row by coalesced loads; after the inverse row FFT
-// each thread sends its 16 outputs X[n2 = j + 256 r] straight to the CTA
-// that owns column n2 (asynchronous remote stores counted on the owner's
-// receive mbarrier), so no CTA reads another's shared memory.  The rows are
-// received into the same buffer the row FFT used (one 34 KiB buffer per
-// CTA, 64 registers: 4 CTAs per SM), so one cluster barrier after the row
-// FFTs both frees every buffer and publishes the receive barriers.  The
-// owner then applies W_L^(-n2 q) from the table and runs its columns.
-template <int LOG2L1>
-__global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
+// Spectrum apply (FUSED_APPLY): G = 2^LOG2G rows of the transform per CTA
+// (256 threads per row), one cluster of CL = L1 / G CTAs per transform.  The
+// spectrum rows arrive by 32 KiB bulk copies, the phase rows by coalesced
+// loads; after the inverse row FFTs each thread writes its 16 outputs X[n2]
+// straight into the shared memory of the CTA that owns column n2 (plain
+// remote stores), so no CTA reads another's shared memory.  The rows are
+// received into the buffers the row FFTs used (one 34 KiB buffer per row,
+// 64 registers: 4 / G CTAs per SM): a first cluster barrier after the row
+// FFTs frees every buffer, a second one after the stores delivers them.
+// The owner then applies W_L^(-n2 q) from the table and runs its columns.
+// Two rows per CTA halve the cluster (8 CTAs at L = 65536): fewer peers per
+// barrier and exchange, which moves the same bytes faster.
+template <int LOG2L1, int LOG2G>
+__global__ void __launch_bounds__(kRowThreads << LOG2G, 4 >> LOG2G) apply_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
-  constexpr int COLS = kRowN / L1;              // columns owned by a CTA
+  constexpr int G = 1 << LOG2G;                 // rows per CTA
+  constexpr int CL = L1 / G;                    // CTAs per transform
+  constexpr int NT = kRowThreads * G;
+  constexpr int COLS = kRowN / CL;              // columns owned by a CTA
   constexpr int PCOLS = COLS;                   // received rows at rpos(c)
-  constexpr int PER = COLS / kRowThreads;       // columns per thread
+  constexpr int PER = COLS / kRowThreads;       // a row thread's output r goes to CTA r / PER
+  constexpr int PERC = COLS / NT;               // columns per thread
+  static_assert(G == 1 || CL > 1, "two rows per CTA need a cluster");
+  static_assert(G == 1 || L1 * COLS <= G * kRowPitch, "received rows fit the row buffers");
   extern __shared__ __align__(128) float2 sm[];
-  float2* A = sm;                               // [kRowPitch] row buffer, then
-  float2* R = sm;                               // [L1][PCOLS] received rows (L1 > 1), column c
+  float2* R = sm;                               // [L1][PCOLS] received rows (CL > 1), column c
                                                 // of row q at q * PCOLS + rpos(c)
-  __shared__ __align__(8) unsigned long long bar_in, bar_r;
+  __shared__ __align__(8) unsigned long long bar_in;
 
-  const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const FftItem I = a.items[blockIdx.x >> LOG2L1];
+  const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const FftItem I = a.items[blockIdx.x >> (LOG2L1 - LOG2G)];
   const int j = threadIdx.x;
-  if (j == 0) {
-    mbar_init(&bar_in, 1);
-    if constexpr (L1 > 1) {
-      mbar_init(&bar_r, 1);
-      mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
-    }
-  }
+  const int h = j / kRowThreads, jj = j % kRowThreads;   // row of the CTA, thread in the row
+  const int k1 = rank * G + h;
+  float2* A = sm + h * kRowPitch;               // this row's buffer
+  if (j == 0) mbar_init(&bar_in, 1);
   __syncthreads();
   if (j == 0) {
-    mbar_expect_tx(&bar_in, kRowN * sizeof(float2));
-    bulk_g2s(A, I.src + (size_t)k1 * kRowN, kRowN * sizeof(float2), &bar_in);
+    mbar_expect_tx(&bar_in, G * kRowN * sizeof(float2));
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      bulk_g2s(sm + g * kRowPitch, I.src + (size_t)(rank * G + g) * kRowN, kRowN * sizeof(float2), &bar_in);
   }
   float2 v[16];
   const float2* prow = I.ptab + (size_t)k1 * kRowN;
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = __ldg(prow + j + 256 * r);
+  for (int r = 0; r < 16; ++r) v[r] = __ldg(prow + jj + 256 * r);
   mbar_wait_bounded(&bar_in, 0, a.err);         // on a timeout: flag raised, keep going
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = cmul(A[j + 256 * r], v[r]);
+  for (int r = 0; r < 16; ++r) v[r] = cmul(A[jj + 256 * r], v[r]);
   __syncthreads();                              // the row FFT overwrites A
-  if constexpr (L1 == 1) row4096_1buf<+1>(v, A, j, a.tw);
-  else row4096_hw<+1, true>(v, A, j, a.tw);     // arrives at the cluster barrier; v[r] at
-                                                // n2 = hw_sigma(j) + 256 r
+  if constexpr (L1 == 1) row4096_1buf<+1>(v, A, jj, a.tw);
+  else row4096_hw<+1, true>(v, A, jj, a.tw);    // arrives at the cluster barrier; v[r] at
+                                                // n2 = hw_sigma(jj) + 256 r
 
   if constexpr (L1 == 1) {
 #pragma unroll
@@ -357,26 +358,26 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
       if (n < I.n_out) __stcs(I.dst + n, v[r]);
     }
   } else {
-    // every peer's row FFT is done with its buffer and its bar_r is
-    // initialised (the release arrive is inside the row FFT)
+    // every peer's row FFTs are done with their buffers (the release arrive
+    // is inside the row FFT)
     cluster_wait<L1>();
-    const uint32_t r_loc = smem_addr(R + k1 * PCOLS + sw16(j));    // rpos(hw_sigma(j))
-    const uint32_t b_loc = smem_addr(&bar_r);
+    const uint32_t r_loc = smem_addr(R + k1 * PCOLS + sw16(jj));   // rpos(hw_sigma(jj))
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      const int owner = r / PER;                // n2 = hw_sigma(j) + 256 r -> owner n2 / COLS
+      const int owner = r / PER;                // n2 = hw_sigma(jj) + 256 r -> owner n2 / COLS
       const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));   // rpos(c + 256 m)
-      st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
+      st_cluster_c64(dsmem_map(r_loc + off, owner), v[r]);
     }
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");   // rows delivered
     const float2* T = a.t4 + kT4Offset(L1);
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int c = j + 256 * p;
-      const int n2 = k1 * COLS + c;
+    for (int p = 0; p < PERC; ++p) {
+      const int c = j + NT * p;
+      const int n2 = rank * COLS + c;
       float2 w[4];
 #pragma unroll
       for (int b = 0; b < LOG2L1; ++b) w[b] = __ldg(T + b * kRowN + n2);   // W_L^(-2^b n2)
-      if (p == 0) mbar_wait_cluster_bounded(&bar_r, 0, a.err);
+      if (p == 0) cluster_wait<L1>();           // every peer's stores into R are visible
       float2 col[L1];
 #pragma unroll
       for (int q = 0; q < L1; ++q) col[q] = R[q * PCOLS + rpos(c)];
@@ -391,26 +392,28 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_kernel(FusedArgs a) {
   }
 }
 
-template <int LOG2L1>
+template <int LOG2L1, int LOG2G>
 cudaError_t launch_apply(const FusedArgs& a, cudaStream_t s) {
   constexpr int L1 = 1 << LOG2L1;
+  constexpr int G = 1 << LOG2G;
+  constexpr int CL = L1 / G;
   if (L1 > 1 && !a.t4) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float2) * kRowPitch;
-  auto k = apply_kernel<LOG2L1>;
+  const size_t smem = sizeof(float2) * kRowPitch * G;
+  auto k = apply_kernel<LOG2L1, LOG2G>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (L1 > 8) {
+  if (CL > 8) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(a.n_items * L1));
-  cfg.blockDim = dim3(kRowThreads);
+  cfg.gridDim = dim3((unsigned)(a.n_items * CL));
+  cfg.blockDim = dim3(kRowThreads * G);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = L1;
+  attr[0].val.clusterDim.x = CL;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -421,13 +424,15 @@ cudaError_t launch_apply(const FusedArgs& a, cudaStream_t s) {
 // Full correction (FUSED_FULL): one row k1 of the transform per CTA, one
 // cluster of L1 CTAs per transform, one padded buffer per CTA.  The forward
 // columns run straight from global memory (zero past n_valid), take
-// W_L^(n2 k1) and go to the row owners by asynchronous remote stores; the
-// forward row, exp(-i phi_k) / L at bin k1 + L1 k2 (regrouped so that each
-// thread owns 16 consecutive k2) and the inverse row follow in the same
-// buffer; the inverse row's outputs go to the column owners the same way,
-// which apply W_L^(-n2 q) and run the inverse columns (out truncated to
-// n_out).  One receive mbarrier serves both exchanges (phases 0 and 1).
-// At L = 4096 one CTA holds the whole transform and takes two buffers.
+// W_L^(n2 k1) and go to the row owners by plain remote stores; the forward
+// row, exp(-i phi_k) / L at bin k1 + L1 k2 (regrouped so that each thread
+// owns 16 consecutive k2) and the inverse row follow in the same buffer; the
+// inverse row's outputs go to the column owners the same way, which apply
+// W_L^(-n2 q) and run the inverse columns (out truncated to n_out).  Cluster
+// barriers order it all: every CTA running before the first remote store,
+// each exchange delivered before it is read, every buffer free before the
+// second exchange overwrites it.  At L = 4096 one CTA holds the whole
+// transform and takes two buffers.
 template <int LOG2L1>
 __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
@@ -438,7 +443,6 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
   extern __shared__ __align__(128) float2 sm[];
   float2* A = sm;                               // [kRowPitch] received row, row FFTs,
   float2* R = sm;                               // then [L1][PCOLS] received inverse rows
-  __shared__ __align__(8) unsigned long long bar_r;
   const int k1 = L1 > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const FftItem I = a.items[blockIdx.x >> LOG2L1];
   const int j = threadIdx.x;
@@ -486,14 +490,8 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
       if (n < I.n_out) __stcs(I.dst + n, v[r]);
     }
   } else {
-    if (j == 0) {
-      mbar_init(&bar_r, 1);
-      mbar_expect_tx(&bar_r, kRowN * sizeof(float2));
-    }
-    __syncthreads();
-    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");   // bar_r published
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");   // this CTA runs
     const float2* T = a.t4 + kT4Offset(L1);
-    const uint32_t b_loc = smem_addr(&bar_r);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int n2 = k1 * COLS + j + 256 * p;
@@ -508,12 +506,13 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
 #pragma unroll
       for (int b = 0; b < LOG2L1; ++b) w[b] = conj_if<+1>(__ldg(T + b * kRowN + n2));
       apply_powers<L1>(col, w);
-      if (p == 0) cluster_wait<L1>();           // every receive barrier is initialised
+      if (p == 0) cluster_wait<L1>();           // every peer runs: its shared memory exists
       const uint32_t dst = smem_addr(A + pad16(n2));
 #pragma unroll
-      for (int q = 0; q < L1; ++q) st_async_c64(dsmem_map(dst, q), col[q], dsmem_map(b_loc, q));
+      for (int q = 0; q < L1; ++q) st_cluster_c64(dsmem_map(dst, q), col[q]);
     }
-    mbar_wait_cluster_bounded(&bar_r, 0, a.err);
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");   // columns delivered
+    cluster_wait<L1>();
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = A[pad16(j + 256 * r)];
     __syncthreads();                            // the row FFT overwrites A
@@ -542,17 +541,16 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cscale(v[r], invL);
     __syncthreads();                            // the inverse row writes A first
-    // phase 1 of bar_r: the inverse rows (phase 0 has completed above)
-    if (j == 0) mbar_expect_tx(&bar_r, L1 * COLS * sizeof(float2));
     row4096_hw<+1, true>(v, A, j, a.tw);        // arrives at the cluster barrier
-    cluster_wait<L1>();                         // every peer's buffer is free, bar_r re-armed
+    cluster_wait<L1>();                         // every peer's buffer is free
     const uint32_t r_loc = smem_addr(R + k1 * PCOLS + sw16(j));    // rpos(hw_sigma(j))
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int owner = r / PER;                // n2 = hw_sigma(j) + 256 r -> owner n2 / COLS
       const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));   // rpos(c + 256 m)
-      st_async_c64(dsmem_map(r_loc + off, owner), v[r], dsmem_map(b_loc, owner));
+      st_cluster_c64(dsmem_map(r_loc + off, owner), v[r]);
     }
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");   // rows delivered
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int c = j + 256 * p;
@@ -560,7 +558,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
       float2 w[4];
 #pragma unroll
       for (int b = 0; b < LOG2L1; ++b) w[b] = __ldg(T + b * kRowN + n2);   // W_L^(-2^b n2)
-      if (p == 0) mbar_wait_cluster_bounded(&bar_r, 1, a.err);
+      if (p == 0) cluster_wait<L1>();           // every peer's stores into R are visible
       float2 col[L1];
 #pragma unroll
       for (int q = 0; q < L1; ++q) col[q] = R[q * PCOLS + rpos(c)];
@@ -671,11 +669,11 @@ cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s) {
   switch (op) {
     case FUSED_APPLY:
       switch (a.log2L) {
-        case 12: return launch_apply<0>(a, s);
-        case 13: return launch_apply<1>(a, s);
-        case 14: return launch_apply<2>(a, s);
-        case 15: return launch_apply<3>(a, s);
-        case 16: return launch_apply<4>(a, s);
+        case 12: return launch_apply<0, 0>(a, s);
+        case 13: return launch_apply<1, 0>(a, s);
+        case 14: return launch_apply<2, 0>(a, s);
+        case 15: return a.apply_rows2 ? launch_apply<3, 1>(a, s) : launch_apply<3, 0>(a, s);
+        case 16: return a.apply_rows2 ? launch_apply<4, 1>(a, s) : launch_apply<4, 0>(a, s);
         default: return cudaErrorInvalidValue;
       }
     case FUSED_FULL:

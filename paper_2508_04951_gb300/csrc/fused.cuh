@@ -10,17 +10,17 @@
 //
 //   FUSED_APPLY : rows of a stored spectrum (bin k1 + L1 k2 at k1*4096 + k2)
 //                 times a phase table in the same layout (already scaled by
-//                 1/L) -> inverse rows -> pushed to the column owners with
-//                 asynchronous remote stores (st.async, completion counted
-//                 on the owner's mbarrier) -> W_L^(-n2 k1) -> inverse
-//                 columns -> out
-//   FUSED_FULL  : y (zero-padded) -> forward columns pushed to the row
-//                 owners (st.async) -> forward rows -> exp(-i phi_k) / L ->
-//                 inverse rows pushed to the column owners (st.async) ->
-//                 inverse columns -> out (truncated to n_out); one padded
-//                 row buffer per CTA
-//   FUSED_SPEC  : y -> forward columns pushed to the row owners (st.async)
-//                 -> forward rows -> spectrum rows
+//                 1/L) -> inverse rows -> written into the column owners'
+//                 shared memory (plain remote stores, delivered by a
+//                 cluster barrier) -> W_L^(-n2 k1) -> inverse columns -> out;
+//                 at L >= 32768 optionally two rows per CTA
+//   FUSED_FULL  : y (zero-padded) -> forward columns written to the row
+//                 owners (remote stores) -> forward rows -> exp(-i phi_k) / L
+//                 -> inverse rows written to the column owners -> inverse
+//                 columns -> out (truncated to n_out); one padded row
+//                 buffer per CTA
+//   FUSED_SPEC  : y -> forward columns written to the row owners (remote
+//                 stores) -> forward rows -> spectrum rows
 #pragma once
 
 #include "fft.cuh"
@@ -39,6 +39,9 @@ struct FusedArgs {
   // for q = 2^b < L1, n2 < 4096, at t4 + kT4Offset(L1) + b * 4096 + n2
   // (the other q are products of these rows).
   const float2* t4;
+  // FUSED_APPLY at L >= 32768: two rows per CTA (512 threads, clusters of
+  // L1 / 2 CTAs) instead of one.
+  int apply_rows2;
 };
 
 // Four-step twiddle rows for L1 = 2, 4, 8, 16: log2(L1) rows of 4096 per L1.

@@ -73,6 +73,14 @@ DC_DEV void st_async_c64(uint32_t raddr, float2 v, uint32_t rbar) {
       : "memory");
 }
 
+// Plain (weak) 8-byte store into a peer's shared memory; a cluster barrier
+// (arrive.release, wait.acquire) makes it visible to the peer.  Without the
+// per-store transaction count of st.async it moves the same bytes markedly
+// faster.
+DC_DEV void st_cluster_c64(uint32_t raddr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(raddr), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // Cluster-scope acquire wait, for barriers completed by peers' st.async.
 DC_DEV bool mbar_try_wait_cluster(unsigned long long* bar, uint32_t parity) {
   uint32_t done;

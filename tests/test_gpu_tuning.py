@@ -76,7 +76,12 @@ def test_forced_batch_schedules_match_oracle(dcg, ctx, schedule):
 
 @pytest.mark.parametrize("n,schedule", [(65536, {"fft": {16: 2}}),
                                         (65536, {"fft": {16: 2}, "chunk": {16: 16 << 20}}),
-                                        (4096, {"fft": {12: 2}})])
+                                        (4096, {"fft": {12: 2}}),
+                                        (65536, {"apply_rows": 1}),    # one row per CTA
+                                        (65536, {"apply_rows": 2}),    # two rows per CTA
+                                        (40000, {"apply_rows": 2}),    # truncated to n_out
+                                        (32768, {"apply_rows": 1}),
+                                        (20000, {"apply_rows": 2})])
 def test_forced_bank_schedules_match_oracle(dcg, ctx, n, schedule):
     import torch
     x = synth.bandlimited_noise(n, synth.rng_for(6, salt=3)).astype(np.complex64)
@@ -132,14 +137,16 @@ def test_autotune_bank_and_plan_use_the_schedule(dcg, ctx):
 
 
 def test_tuning_set_rejects_bad_schedules(dcg, ctx):
-    for bad in ({"resample_q": 6}, {"fft": {17: 1}}, {"fft": {14: 3}}, {"chunk": {18: -2}}):
+    for bad in ({"resample_q": 6}, {"fft": {17: 1}}, {"fft": {14: 3}}, {"chunk": {18: -2}},
+                {"apply_rows": 3}, {"apply_rows": -1}):
         with pytest.raises(dcg.DcError):
             dcg.dc_tuning_set(ctx, bad)
     assert dcg.dc_tuning_get(ctx)["fft"] == {}
 
 
 def test_schedule_cache_round_trip(dcg, ctx, tmp_path, monkeypatch):
-    sched = {"resample_q": 4, "resample_tc": 2, "fft": {13: 2, 16: 1}, "chunk": {17: 64 << 20}}
+    sched = {"resample_q": 4, "resample_tc": 2, "apply_rows": 1, "fft": {13: 2, 16: 1},
+             "chunk": {17: 64 << 20}}
     dcg.dc_tuning_set(ctx, sched)
     path = str(tmp_path / "sched.json")
     dcg.dc_tuning_save(ctx, path)
@@ -148,8 +155,8 @@ def test_schedule_cache_round_trip(dcg, ctx, tmp_path, monkeypatch):
     other = dcg.Context(0)
     dcg.dc_tuning_load(other, path)
     got = dcg.dc_tuning_get(other)
-    assert (got["resample_q"], got["resample_tc"], got["fft"], got["chunk"]) == \
-        (4, 2, {13: 2, 16: 1}, {17: 64 << 20})
+    assert (got["resample_q"], got["resample_tc"], got["apply_rows"], got["fft"], got["chunk"]) == \
+        (4, 2, 1, {13: 2, 16: 1}, {17: 64 << 20})
     other.close()
     # a context created with DC_TUNING_CACHE set starts from that file
     monkeypatch.setenv("DC_TUNING_CACHE", path)
