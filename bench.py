@@ -62,10 +62,10 @@ METRIC = "corrected Msamples/s and p50/p99 pulse latency vs plain path at stated
 UNIT = "Msamples/s"
 ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
 # DRAM bytes (read + write) per launch of the kernel at the full workload, from
-# one ncu capture of the full-size launch (dram__bytes_read.sum 146,380,288 +
-# dram__bytes_write.sum 2,086,405,120).  Cleared whenever the kernel changes
+# one ncu capture of the full-size launch (dram__bytes_read.sum 146,799,360 +
+# dram__bytes_write.sum 2,085,873,664).  Cleared whenever the kernel changes
 # after the capture.
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 146380288.0 + 2086405120.0}
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 146799360.0 + 2085873664.0}
 
 
 def load_peaks() -> tuple[float, str]:
