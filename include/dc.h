@@ -398,11 +398,14 @@ DC_API dc_status dc_serve_counters(dc_server* server, dc_serve_info* out);
  *               the pulse's Hankel tiles with per-range-rate tap weights and
  *               their derivatives, fp16 hi/lo operands; used where the range
  *               rates allow it), 2 = the CUDA-core kernel;
- *   apply_rows  the cluster-fused spectrum apply (bank, L >= 32768): 1 = one
- *               4096-point row per CTA (clusters of L / 4096 CTAs), 2 = two
- *               rows per CTA (clusters of half that size).
+ *   apply_kind  the bank's spectrum apply (factors + inverse transform) for
+ *               8192 <= L <= 65536: 1 = cluster-fused, one 4096-point row per
+ *               CTA (clusters of L / 4096 CTAs); 2 = cluster-fused, two rows
+ *               per CTA (L >= 32768); 3 = rows and columns as tasks of one
+ *               persistent grid meeting in an L2-resident scratch (no
+ *               clusters).
  * 0 in any field means the library's built-in rule (tensor cores where
- * eligible for resample_tc, one row per CTA for apply_rows). */
+ * eligible for resample_tc, one row per CTA for apply_kind). */
 typedef struct {
   int resample_q;
   int fft[21];
@@ -411,7 +414,7 @@ typedef struct {
   double ms_best;       /* the same call under the chosen schedule              */
   int candidates;       /* schedules timed                                      */
   int resample_tc;
-  int apply_rows;
+  int apply_kind;
 } dc_tuning;
 
 /* Measure the schedule choices the call meets on its own data (each
@@ -435,7 +438,7 @@ DC_API dc_status dc_tuning_set(dc_ctx* ctx, const dc_tuning* t);
 
 /* Schedule cache: dc_tuning_save writes the context's schedule to `path` as
  * a small JSON object ({"format": "dc_tuning/1", "resample_q": .., "resample_tc":
- * .., "apply_rows": .., "fft": {"<m>": ..}, "chunk": {"<m>": ..}}); dc_tuning_load reads such a
+ * .., "apply_kind": .., "fft": {"<m>": ..}, "chunk": {"<m>": ..}}); dc_tuning_load reads such a
  * file and applies it as dc_tuning_set would (DC_EINVAL for a missing or
  * malformed file or an invalid schedule).  With the environment variable
  * DC_TUNING_CACHE naming a file, dc_create loads it when it exists and every

@@ -52,7 +52,7 @@ class DcTuning(ctypes.Structure):
     _fields_ = [("resample_q", ctypes.c_int), ("fft", ctypes.c_int * 21),
                 ("chunk", ctypes.c_longlong * 21), ("ms_default", ctypes.c_double),
                 ("ms_best", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("resample_tc", ctypes.c_int), ("apply_rows", ctypes.c_int)]
+                ("resample_tc", ctypes.c_int), ("apply_kind", ctypes.c_int)]
 
 
 class DcServeInfo(ctypes.Structure):
@@ -526,7 +526,7 @@ def dc_serve_stop(srv: Server) -> None:
 # ----------------------------------------------------------- autotuning
 
 def _tuning_dict(t: DcTuning) -> dict:
-    return {"resample_q": t.resample_q, "resample_tc": t.resample_tc, "apply_rows": t.apply_rows,
+    return {"resample_q": t.resample_q, "resample_tc": t.resample_tc, "apply_kind": t.apply_kind,
             "fft": {m: t.fft[m] for m in range(21) if t.fft[m]},
             "chunk": {m: t.chunk[m] for m in range(21) if t.chunk[m]},
             "ms_default": t.ms_default, "ms_best": t.ms_best, "candidates": t.candidates}
@@ -564,7 +564,7 @@ def dc_tuning_get(ctx: Context) -> dict:
 
 
 def dc_tuning_set(ctx: Context, schedule: dict | None) -> None:
-    """Replace the context's schedule ({"resample_q", "resample_tc", "apply_rows",
+    """Replace the context's schedule ({"resample_q", "resample_tc", "apply_kind",
     "fft": {m: v}, "chunk": {m: bytes}});
     None restores the built-in rules."""
     if schedule is None:
@@ -573,7 +573,7 @@ def dc_tuning_set(ctx: Context, schedule: dict | None) -> None:
     t = DcTuning()
     t.resample_q = int(schedule.get("resample_q", 0))
     t.resample_tc = int(schedule.get("resample_tc", 0))
-    t.apply_rows = int(schedule.get("apply_rows", 0))
+    t.apply_kind = int(schedule.get("apply_kind", 0))
     for m, v in schedule.get("fft", {}).items():
         t.fft[int(m)] = int(v)
     for m, v in schedule.get("chunk", {}).items():

@@ -70,7 +70,8 @@ struct dc_ctx {
     long long chunk[21] = {};  // three-pass intermediate bytes per chunk (-1: whole class)
     int fft[21] = {};          // 4096 <= L <= 65536: 1 cluster-fused, 2 three passes
     int rs_tc = 0;             // bank resampling: 1 tensor cores (where eligible), 2 CUDA cores
-    int apply_rows = 0;        // spectrum apply at L >= 32768: rows per CTA, 1 or 2
+    int apply_kind = 0;        // spectrum apply: 1 cluster, one row per CTA; 2 cluster, two rows
+                               // per CTA (L >= 32768); 3 two passes through L2 (L >= 8192)
   } tune;
   std::recursive_mutex mu;
 };
@@ -109,7 +110,17 @@ bool use_fused(const dc_ctx* c, int log2L) { return fused_L(log2L) && c->tune.ff
 // Two rows per CTA in the spectrum-apply kernel (L >= 32768 only).  The
 // built-in rule keeps one: on the 256 x 16 bank at L = 65536 two rows (8-CTA
 // clusters, 2 CTAs per SM) ran 1.46 ms against 1.36 ms.
-bool apply_rows2(const dc_ctx* c, int log2L) { return log2L >= 15 && c->tune.apply_rows == 2; }
+bool apply_rows2(const dc_ctx* c, int log2L) { return log2L >= 15 && c->tune.apply_kind == 2; }
+// The spectrum apply in two passes through an L2-resident scratch (no
+// clusters), for 8192 <= L <= 65536.
+bool apply_l2(const dc_ctx* c, int log2L) { return log2L >= 13 && c->tune.apply_kind == 3; }
+// Transforms per chunk of the two-pass apply: 8 MiB of them (256 row tasks),
+// so that the scratch (kApplyL2Slots chunks, 32 MiB) stays in L2 beside the
+// spectra and factor tables.
+int apply_l2_chunk(int log2L, size_t n_pairs) {
+  const size_t per = (size_t)8 << 20 >> (log2L + 3);
+  return (int)std::max<size_t>(1, std::min(per, n_pairs));
+}
 
 // Transforms per chunk of a three-pass class.  The tuned intermediate size
 // wins; else `dflt` bytes (0: the whole class at once -- the batch, whose
@@ -1060,8 +1071,12 @@ dc_status bank_impl(dc_ctx* c, const dc_c64* x, long long n, const dc_c64* rep, 
   const size_t s_at = ar.take((size_t)n_sp * L * sizeof(float2));
   const size_t t_at =
       ar.take(fused ? 0 : (size_t)std::max(chunk, four ? n_sp : 0) * L * sizeof(float2));
-  if ((st = ensure_ws(c, ar.off))) return st;
   const size_t n_pairs = (size_t)n_v * n_tec;
+  const bool l2 = fused && apply_l2(c, log2L);
+  const int l2_chunk = l2 ? apply_l2_chunk(log2L, n_pairs) : 0;
+  const size_t q_at = ar.take(l2 ? (size_t)kApplyL2Slots * l2_chunk * L * sizeof(float2) : 0);
+  const size_t k_at = ar.take(l2 ? (1 + 2 * n_pairs) * sizeof(int) : 0);
+  if ((st = ensure_ws(c, ar.off))) return st;
   if ((st = ensure_items(c, items_bytes_for(n_pairs * 2 + n_sp * 6 + n_tec)))) return st;
   char* ws = c->ws;
   float2* Yr = reinterpret_cast<float2*>(ws + y_at);
@@ -1135,6 +1150,13 @@ dc_status bank_impl(dc_ctx* c, const dc_c64* x, long long n, const dc_c64* rep, 
     if ((st = upload(c, ap, item_at, s, &dev))) return st;
     FusedArgs a{dev, (int)n_pairs, log2L, c->tw, c->err, c->t4};
     a.apply_rows2 = apply_rows2(c, log2L);
+    if (l2) {
+      a.scratch = reinterpret_cast<float2*>(ws + q_at);
+      a.ctr = reinterpret_cast<int*>(ws + k_at);
+      a.chunk = l2_chunk;
+      if ((e = cudaMemsetAsync(a.ctr, 0, (1 + 2 * n_pairs) * sizeof(int), s)) != cudaSuccess)
+        return cuda_fail(c, e, "apply counters");
+    }
     Phase ph(c, PH_FUSED_APPLY, s, (long long)n_pairs * n_out);
     if ((e = launch_fused(FUSED_APPLY, a, s)) != cudaSuccess) return cuda_fail(c, e, "apply launch");
     return DC_OK;
@@ -1504,20 +1526,20 @@ extern "C" dc_status dc_plan_destroy(dc_plan* p) {
 namespace {
 
 struct Choice {
-  int kind;   // 0 resample_q, 1 fft[m], 2 chunk[m], 3 bank resampling engine, 4 apply rows per CTA
+  int kind;   // 0 resample_q, 1 fft[m], 2 chunk[m], 3 bank resampling engine, 4 spectrum-apply kind
   int m;
   std::vector<long long> values;
 };
 
 long long tune_get(const dc_ctx* c, const Choice& d) {
-  if (d.kind == 4) return c->tune.apply_rows;
+  if (d.kind == 4) return c->tune.apply_kind;
   if (d.kind == 3) return c->tune.rs_tc;
   if (d.kind == 0) return c->tune.rs_q;
   if (d.kind == 1) return c->tune.fft[d.m];
   return c->tune.chunk[d.m];
 }
 void tune_set(dc_ctx* c, const Choice& d, long long v) {
-  if (d.kind == 4) c->tune.apply_rows = (int)v;
+  if (d.kind == 4) c->tune.apply_kind = (int)v;
   else if (d.kind == 3) c->tune.rs_tc = (int)v;
   else if (d.kind == 0) c->tune.rs_q = (int)v;
   else if (d.kind == 1) c->tune.fft[d.m] = (int)v;
@@ -1551,7 +1573,7 @@ void tuning_out(const dc_ctx* c, dc_tuning* t) {
   *t = dc_tuning{};
   t->resample_q = c->tune.rs_q;
   t->resample_tc = c->tune.rs_tc;
-  t->apply_rows = c->tune.apply_rows;
+  t->apply_kind = c->tune.apply_kind;
   for (int m = 0; m <= 20; ++m) {
     t->fft[m] = c->tune.fft[m];
     t->chunk[m] = c->tune.chunk[m];
@@ -1664,7 +1686,8 @@ extern "C" dc_status dc_autotune_bank(dc_ctx* c, const dc_c64* x, long long n, c
   if (o.mode == DC_WINDOWED && o.taps == 32 && !o.carrier_shift) ch.push_back({3, 0, {1, 2}});
   if (o.mode == DC_WINDOWED && o.taps == 32 && q8) ch.push_back({0, 0, {8, 4}});
   class_choices(ch, log2_ceil(n_out), (size_t)n_v * n_tec);
-  if (log2_ceil(n_out) >= 15 && log2_ceil(n_out) <= 16) ch.push_back({4, 0, {2, 1}});
+  if (log2_ceil(n_out) >= 13 && log2_ceil(n_out) <= 16)
+    ch.push_back({4, 0, log2_ceil(n_out) >= 15 ? std::vector<long long>{1, 2, 3} : std::vector<long long>{1, 3}});
   cudaSetDevice(c->device);
   cudaStream_t s = S(stream);
   return autotune(
@@ -1689,8 +1712,8 @@ extern "C" dc_status dc_tuning_set(dc_ctx* c, const dc_tuning* t) {
     return fail(c, DC_EINVAL, "resample_q must be 0, 4 or 8");
   if (t->resample_tc < 0 || t->resample_tc > 2)
     return fail(c, DC_EINVAL, "resample_tc must be 0, 1 or 2");
-  if (t->apply_rows < 0 || t->apply_rows > 2)
-    return fail(c, DC_EINVAL, "apply_rows must be 0, 1 or 2");
+  if (t->apply_kind < 0 || t->apply_kind > 3)
+    return fail(c, DC_EINVAL, "apply_kind must be 0, 1, 2 or 3");
   for (int m = 0; m <= 20; ++m) {
     if (t->fft[m] < 0 || t->fft[m] > 2 || (t->fft[m] && (m < 12 || m > 16)))
       return fail(c, DC_EINVAL, "fft[%d] must be 0, 1 or 2 (and 0 outside 4096 <= L <= 65536)", m);
@@ -1698,7 +1721,7 @@ extern "C" dc_status dc_tuning_set(dc_ctx* c, const dc_tuning* t) {
   }
   c->tune.rs_q = t->resample_q;
   c->tune.rs_tc = t->resample_tc;
-  c->tune.apply_rows = t->apply_rows;
+  c->tune.apply_kind = t->apply_kind;
   for (int m = 0; m <= 20; ++m) {
     c->tune.fft[m] = t->fft[m];
     c->tune.chunk[m] = t->chunk[m];
@@ -1733,14 +1756,14 @@ dc_status dc_internal_correct_batch_ws(dc_ctx* c, const dc_c64* in, dc_c64* out,
 // ------------------------------------------------------ schedule cache
 // The context's schedule as a small JSON object, e.g.
 //   {"format": "dc_tuning/1", "resample_q": 0, "resample_tc": 1,
-//    "apply_rows": 0, "fft": {"16": 1}, "chunk": {"17": 67108864}}
+//    "apply_kind": 0, "fft": {"16": 1}, "chunk": {"17": 67108864}}
 // (only non-zero entries of fft / chunk are written).
 namespace {
 
 std::string tuning_json(const dc_ctx* c) {
   std::string s = "{\"format\": \"dc_tuning/1\", \"resample_q\": " + std::to_string(c->tune.rs_q) +
                   ", \"resample_tc\": " + std::to_string(c->tune.rs_tc) +
-                  ", \"apply_rows\": " + std::to_string(c->tune.apply_rows) + ", \"fft\": {";
+                  ", \"apply_kind\": " + std::to_string(c->tune.apply_kind) + ", \"fft\": {";
   bool first = true;
   for (int m = 0; m <= 20; ++m)
     if (c->tune.fft[m]) {
@@ -1812,10 +1835,10 @@ bool parse_tuning(const std::string& text, dc_tuning& t) {
       std::string f;
       if (!in.str(f)) return false;
       format_ok = f == "dc_tuning/1";
-    } else if (k == "resample_q" || k == "resample_tc" || k == "apply_rows") {
+    } else if (k == "resample_q" || k == "resample_tc" || k == "apply_kind") {
       long long v;
       if (!in.num(v)) return false;
-      (k == "resample_q" ? t.resample_q : k == "resample_tc" ? t.resample_tc : t.apply_rows) = (int)v;
+      (k == "resample_q" ? t.resample_q : k == "resample_tc" ? t.resample_tc : t.apply_kind) = (int)v;
     } else if (k == "fft" || k == "chunk") {
       if (!parse_map(in, k == "fft" ? fft : chunk)) return false;
     } else {

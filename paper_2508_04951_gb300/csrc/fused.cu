@@ -1,4 +1,5 @@
 // Cluster-fused FFT correction kernels; see fused.cuh for the data flow.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "fused.cuh"
@@ -421,6 +422,160 @@ cudaError_t launch_apply(const FusedArgs& a, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, k, a);
 }
 
+// Spectrum apply in two passes through L2 (FUSED_APPLY with a.scratch set):
+// no cluster.  A persistent grid takes tasks from one global queue in a
+// fixed order.  A row task transforms one 4096-point row of one transform
+// (spectrum row times factor row, inverse row) into a scratch slot; a column
+// task reads 4096 / L1 columns of one transform back from its slot, applies
+// W_L^(-n2 q) and runs the length-L1 inverse columns into the output.  The
+// transforms go in chunks of P = a.chunk: the queue alternates the rows of
+// chunk i and the columns of chunk i - kApplyLag, and the scratch holds
+// (kApplyLag + 2) P transforms (slot = transform mod that), small enough to
+// stay in L2 between the passes, so DRAM sees the output once, as with the
+// cluster kernel, but no cluster barrier or distributed-shared-memory
+// exchange is needed.  A task is counted done by one release reduction
+// after a CTA barrier; a column task waits until the L1 rows of its
+// transform are counted, a row task until the columns of the slot's
+// previous transform are (one thread polls with acquire loads, the others
+// wait at a CTA barrier).  The lag keeps both waits on
+// tasks queued several blocks earlier (a grid holds about 2.4 blocks of
+// tasks at once), so they rarely wait at all.  Every wait is on tasks taken
+// from the queue earlier, by CTAs already running, so the order cannot
+// deadlock; each wait is bounded (error flag 1 when it runs out, and the
+// task goes on).  Counters (a.ctr: queue head, then rows done and columns
+// done per transform) start at zero.
+constexpr int kApplyLag = kApplyL2Slots - 2;
+
+DC_DEV int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Release add: the writes this thread has made or observed (a CTA barrier
+// before it covers the whole CTA's) become visible before the count.
+DC_DEV void red_release_gpu(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: poll *p until it reaches `want`, for about a second at most.
+DC_DEV void wait_count(const int* p, int want, int* err) {
+  for (int i = 0; i < (1 << 24); ++i) {
+    if (ld_acquire_gpu(p) >= want) return;
+    __nanosleep(64);
+  }
+  atomicExch(err, 1);
+}
+
+template <int LOG2L1>
+__global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
+  constexpr int L1 = 1 << LOG2L1;
+  constexpr int COLS = kRowN / L1;              // columns of a column task
+  constexpr int PER = COLS / kRowThreads;       // columns per thread
+  extern __shared__ __align__(128) float2 sm[]; // [kRowPitch] the row buffer
+  __shared__ __align__(8) unsigned long long bar_in;
+  __shared__ int s_task[2];
+  const int j = threadIdx.x;
+  const int P = a.chunk;
+  const int n_chunks = (a.n_items + P - 1) / P;
+  const int per_block = P * L1;                 // the rows (or columns) of one chunk
+  // block 2i: rows of chunk i; block 2i + 1: columns of chunk i - kApplyLag
+  const int n_tasks = 2 * (n_chunks + kApplyLag) * per_block;
+  const int n_slots = (kApplyLag + 2) * P;
+  int* head = a.ctr;
+  int* row_done = a.ctr + 1;
+  int* col_done = a.ctr + 1 + a.n_items;
+  const size_t slot_elems = (size_t)L1 * kRowN;
+  int t_next = 0;                               // thread 0: the task taken ahead
+  if (j == 0) {
+    mbar_init(&bar_in, 1);
+    s_task[0] = atomicAdd(head, 1);
+  }
+  uint32_t phase = 0;
+  for (int it = 0;; ++it) {
+    __syncthreads();                            // s_task; the last task's reads of sm are done
+    const int t = s_task[it & 1];
+    if (t >= n_tasks) break;
+    if (j == 0) t_next = atomicAdd(head, 1);    // used at the end of this task
+    const int b = t / per_block, w = t % per_block;
+    const bool is_col = b & 1;
+    const int chunk = is_col ? (b >> 1) - kApplyLag : b >> 1;
+    const int p = chunk * P + w / L1;
+    const int rq = w % L1;                      // row k1, or column block q
+    if (chunk >= 0 && chunk < n_chunks && p < a.n_items) {
+      const FftItem I = a.items[p];
+      float2* slot = a.scratch + (size_t)(p % n_slots) * slot_elems;
+      if (!is_col) {
+        if (j == 0) {                           // the spectrum row first: its copy overlaps the rest
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // after the last generic reads
+          mbar_expect_tx(&bar_in, kRowN * sizeof(float2));
+          bulk_g2s(sm, I.src + (size_t)rq * kRowN, kRowN * sizeof(float2), &bar_in);
+        }
+        float2 v[16];
+        const float2* prow = I.ptab + (size_t)rq * kRowN;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = __ldg(prow + j + 256 * r);
+        mbar_wait_bounded(&bar_in, phase, a.err);
+        phase ^= 1;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = cmul(sm[j + 256 * r], v[r]);
+        // the slot is free; the CTA barrier orders thread 0's wait before
+        // every thread's stores (the others wait there, polling nothing)
+        if (j == 0 && p >= n_slots) wait_count(col_done + p - n_slots, L1, a.err);
+        __syncthreads();                        // also: the row FFT overwrites sm
+        row4096_1buf<+1>(v, sm, j, a.tw);       // v[r] = Y[j + 256 r]
+        float2* yrow = slot + (size_t)rq * kRowN;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) __stcg(yrow + j + 256 * r, v[r]);
+        __syncthreads();
+        if (j == 0) red_release_gpu(row_done + p, 1);   // every thread's row stores first
+      } else {
+        if (j == 0) wait_count(row_done + p, L1, a.err);
+        __syncthreads();
+        const float2* T = a.t4 + kT4Offset(L1);
+#pragma unroll
+        for (int pp = 0; pp < PER; ++pp) {
+          const int n2 = rq * COLS + j + 256 * pp;
+          float2 w4[4];
+#pragma unroll
+          for (int bb = 0; bb < LOG2L1; ++bb) w4[bb] = __ldg(T + bb * kRowN + n2);   // W_L^(-2^b n2)
+          float2 col[L1];
+#pragma unroll
+          for (int q = 0; q < L1; ++q) col[q] = __ldcg(slot + (size_t)q * kRowN + n2);
+          apply_powers<L1>(col, w4);
+          dft<L1, +1>(col);
+#pragma unroll
+          for (int n1 = 0; n1 < L1; ++n1) {
+            const int n = n2 + kRowN * n1;
+            if (n < I.n_out) __stcs(I.dst + n, col[n1]);
+          }
+        }
+        __syncthreads();
+        if (j == 0) red_release_gpu(col_done + p, 1);   // every thread's slot reads first
+      }
+    }
+    if (j == 0) s_task[(it + 1) & 1] = t_next;
+  }
+}
+
+template <int LOG2L1>
+cudaError_t launch_apply_l2(const FusedArgs& a, cudaStream_t s) {
+  if (!a.t4 || !a.scratch || !a.ctr || a.chunk < 1) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * kRowPitch;
+  auto k = apply_l2_kernel<LOG2L1>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kRowThreads, smem)) != cudaSuccess)
+    return e;
+  const long long tasks = 2LL * (a.n_items + (long long)kApplyLag * a.chunk) * (1 << LOG2L1);
+  const int grid = (int)std::max(1LL, std::min<long long>((long long)sms * std::max(per_sm, 1), tasks));
+  k<<<grid, kRowThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 // Full correction (FUSED_FULL): one row k1 of the transform per CTA, one
 // cluster of L1 CTAs per transform, one padded buffer per CTA.  The forward
 // columns run straight from global memory (zero past n_valid), take
@@ -670,10 +825,12 @@ cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s) {
     case FUSED_APPLY:
       switch (a.log2L) {
         case 12: return launch_apply<0, 0>(a, s);
-        case 13: return launch_apply<1, 0>(a, s);
-        case 14: return launch_apply<2, 0>(a, s);
-        case 15: return a.apply_rows2 ? launch_apply<3, 1>(a, s) : launch_apply<3, 0>(a, s);
-        case 16: return a.apply_rows2 ? launch_apply<4, 1>(a, s) : launch_apply<4, 0>(a, s);
+        case 13: return a.scratch ? launch_apply_l2<1>(a, s) : launch_apply<1, 0>(a, s);
+        case 14: return a.scratch ? launch_apply_l2<2>(a, s) : launch_apply<2, 0>(a, s);
+        case 15: return a.scratch ? launch_apply_l2<3>(a, s)
+                       : a.apply_rows2 ? launch_apply<3, 1>(a, s) : launch_apply<3, 0>(a, s);
+        case 16: return a.scratch ? launch_apply_l2<4>(a, s)
+                       : a.apply_rows2 ? launch_apply<4, 1>(a, s) : launch_apply<4, 0>(a, s);
         default: return cudaErrorInvalidValue;
       }
     case FUSED_FULL:

@@ -13,7 +13,9 @@
 //                 1/L) -> inverse rows -> written into the column owners'
 //                 shared memory (plain remote stores, delivered by a
 //                 cluster barrier) -> W_L^(-n2 k1) -> inverse columns -> out;
-//                 at L >= 32768 optionally two rows per CTA
+//                 at L >= 32768 optionally two rows per CTA; or, without
+//                 clusters, rows and columns as tasks of one persistent grid
+//                 meeting in an L2-resident scratch
 //   FUSED_FULL  : y (zero-padded) -> forward columns written to the row
 //                 owners (remote stores) -> forward rows -> exp(-i phi_k) / L
 //                 -> inverse rows written to the column owners -> inverse
@@ -42,6 +44,12 @@ struct FusedArgs {
   // FUSED_APPLY at L >= 32768: two rows per CTA (512 threads, clusters of
   // L1 / 2 CTAs) instead of one.
   int apply_rows2;
+  // FUSED_APPLY at L >= 8192 in two passes through L2 instead of clusters:
+  // scratch for kApplyL2Slots * chunk transforms (L float2 each), counters
+  // (1 + 2 * n_items ints, zero at launch), transforms per chunk.
+  float2* scratch;
+  int* ctr;
+  int chunk;
 };
 
 // Four-step twiddle rows for L1 = 2, 4, 8, 16: log2(L1) rows of 4096 per L1.
@@ -50,6 +58,10 @@ __host__ __device__ constexpr int kT4Offset(int l1) {
   return kT4Log2(l1) * (kT4Log2(l1) - 1) / 2 * 4096;
 }
 constexpr int kT4Size = 10 * 4096;
+
+// Scratch slots of the two-pass apply, in chunks (the queue's lag between a
+// chunk's rows and its columns, plus two).
+constexpr int kApplyL2Slots = 4;
 
 // Launch; returns cudaErrorInvalidValue for L outside [4096, 65536].
 cudaError_t launch_fused(int op, const FusedArgs& a, cudaStream_t s);

@@ -77,11 +77,16 @@ def test_forced_batch_schedules_match_oracle(dcg, ctx, schedule):
 @pytest.mark.parametrize("n,schedule", [(65536, {"fft": {16: 2}}),
                                         (65536, {"fft": {16: 2}, "chunk": {16: 16 << 20}}),
                                         (4096, {"fft": {12: 2}}),
-                                        (65536, {"apply_rows": 1}),    # one row per CTA
-                                        (65536, {"apply_rows": 2}),    # two rows per CTA
-                                        (40000, {"apply_rows": 2}),    # truncated to n_out
-                                        (32768, {"apply_rows": 1}),
-                                        (20000, {"apply_rows": 2})])
+                                        (65536, {"apply_kind": 1}),    # one row per CTA
+                                        (65536, {"apply_kind": 2}),    # two rows per CTA
+                                        (40000, {"apply_kind": 2}),    # truncated to n_out
+                                        (32768, {"apply_kind": 1}),
+                                        (20000, {"apply_kind": 2}),
+                                        (65536, {"apply_kind": 3}),    # two passes through L2
+                                        (40000, {"apply_kind": 3}),
+                                        (20000, {"apply_kind": 3}),
+                                        (10000, {"apply_kind": 3}),
+                                        (5000, {"apply_kind": 3})])
 def test_forced_bank_schedules_match_oracle(dcg, ctx, n, schedule):
     import torch
     x = synth.bandlimited_noise(n, synth.rng_for(6, salt=3)).astype(np.complex64)
@@ -96,6 +101,33 @@ def test_forced_bank_schedules_match_oracle(dcg, ctx, n, schedule):
     for i in range(len(v)):
         for t in range(len(tec)):
             assert rel(out[i, t], ref[i, t]) <= TOL
+
+
+@pytest.mark.parametrize("n,n_v,n_tec", [(65536, 12, 8), (16384, 40, 16)])
+def test_two_pass_apply_reuses_its_scratch_slots(dcg, ctx, n, n_v, n_tec):
+    # more transforms than the scratch holds (two chunks of 32 at L = 65536,
+    # of 128 at L = 16384): slots are reused after their columns are done;
+    # every pair agrees with the cluster kernel, sampled pairs with the oracle
+    import torch
+    x = synth.bandlimited_noise(n, synth.rng_for(6, salt=7)).astype(np.complex64)
+    v = np.linspace(-7900.0, 7900.0, n_v)
+    tec = np.linspace(5.0, 150.0, n_tec)
+    xd = torch.from_numpy(x).cuda()
+    outs = {}
+    for kind in (1, 3):
+        dcg.dc_tuning_set(ctx, {"apply_kind": kind})
+        od = torch.full((n_v * n_tec * n,), complex(7.0, -7.0), dtype=torch.complex64, device="cuda:0")
+        dcg.correct_bank(ctx, xd, v, tec, od, 20e6, 1e9)
+        dcg.dc_check(ctx)
+        outs[kind] = od.cpu().numpy().reshape(n_v, n_tec, n)
+    dcg.dc_tuning_set(ctx, None)
+    for i in range(n_v):
+        for t in range(n_tec):
+            assert rel(outs[3][i, t], outs[1][i, t]) <= 1e-6, (i, t)
+    ref = oracle.correct_bank(x.astype(np.complex128), 20e6, 1e9, v[[0, n_v - 1]], tec[[0, n_tec - 1]])
+    for a, i in enumerate((0, n_v - 1)):
+        for b, t in enumerate((0, n_tec - 1)):
+            assert rel(outs[3][i, t], ref[a, b]) <= TOL
 
 
 def test_autotune_batch_keeps_the_fastest_and_correct(dcg, ctx):
@@ -138,14 +170,14 @@ def test_autotune_bank_and_plan_use_the_schedule(dcg, ctx):
 
 def test_tuning_set_rejects_bad_schedules(dcg, ctx):
     for bad in ({"resample_q": 6}, {"fft": {17: 1}}, {"fft": {14: 3}}, {"chunk": {18: -2}},
-                {"apply_rows": 3}, {"apply_rows": -1}):
+                {"apply_kind": 4}, {"apply_kind": -1}):
         with pytest.raises(dcg.DcError):
             dcg.dc_tuning_set(ctx, bad)
     assert dcg.dc_tuning_get(ctx)["fft"] == {}
 
 
 def test_schedule_cache_round_trip(dcg, ctx, tmp_path, monkeypatch):
-    sched = {"resample_q": 4, "resample_tc": 2, "apply_rows": 1, "fft": {13: 2, 16: 1},
+    sched = {"resample_q": 4, "resample_tc": 2, "apply_kind": 1, "fft": {13: 2, 16: 1},
              "chunk": {17: 64 << 20}}
     dcg.dc_tuning_set(ctx, sched)
     path = str(tmp_path / "sched.json")
@@ -155,7 +187,7 @@ def test_schedule_cache_round_trip(dcg, ctx, tmp_path, monkeypatch):
     other = dcg.Context(0)
     dcg.dc_tuning_load(other, path)
     got = dcg.dc_tuning_get(other)
-    assert (got["resample_q"], got["resample_tc"], got["apply_rows"], got["fft"], got["chunk"]) == \
+    assert (got["resample_q"], got["resample_tc"], got["apply_kind"], got["fft"], got["chunk"]) == \
         (4, 2, 1, {13: 2, 16: 1}, {17: 64 << 20})
     other.close()
     # a context created with DC_TUNING_CACHE set starts from that file
