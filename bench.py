@@ -62,10 +62,10 @@ METRIC = "corrected Msamples/s and p50/p99 pulse latency vs plain path at stated
 UNIT = "Msamples/s"
 ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
 # DRAM bytes (read + write) per launch of the kernel at the full workload, from
-# one ncu capture of the full-size launch (dram__bytes_read.sum 146,799,360 +
-# dram__bytes_write.sum 2,085,873,664).  Cleared whenever the kernel changes
-# after the capture.
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 146799360.0 + 2085873664.0}
+# one ncu capture of the full-size launch (the two-pass apply kernel:
+# dram__bytes_read.sum 176,610,304 + dram__bytes_write.sum 2,208,197,888).
+# Cleared whenever the kernel changes after the capture.
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 176610304.0 + 2208197888.0}
 
 
 def load_peaks() -> tuple[float, str]:

@@ -405,7 +405,8 @@ DC_API dc_status dc_serve_counters(dc_server* server, dc_serve_info* out);
  *               persistent grid meeting in an L2-resident scratch (no
  *               clusters).
  * 0 in any field means the library's built-in rule (tensor cores where
- * eligible for resample_tc, one row per CTA for apply_kind). */
+ * eligible for resample_tc; for apply_kind two passes at L = 65536, one row
+ * per CTA below). */
 typedef struct {
   int resample_q;
   int fft[21];

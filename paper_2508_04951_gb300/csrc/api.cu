@@ -112,8 +112,13 @@ bool use_fused(const dc_ctx* c, int log2L) { return fused_L(log2L) && c->tune.ff
 // clusters, 2 CTAs per SM) ran 1.46 ms against 1.36 ms.
 bool apply_rows2(const dc_ctx* c, int log2L) { return log2L >= 15 && c->tune.apply_kind == 2; }
 // The spectrum apply in two passes through an L2-resident scratch (no
-// clusters), for 8192 <= L <= 65536.
-bool apply_l2(const dc_ctx* c, int log2L) { return log2L >= 13 && c->tune.apply_kind == 3; }
+// clusters), for 8192 <= L <= 65536.  The built-in rule takes it at
+// L = 65536, where the 16-CTA clusters' exchange costs more than the second
+// pass through L2 (256 x 16 bank: 1.19 vs 1.36 ms); below, the smaller
+// clusters win (L = 32768: 0.60 vs 0.57 ms; 16384: 0.30 vs 0.27 ms).
+bool apply_l2(const dc_ctx* c, int log2L) {
+  return log2L >= 13 && (c->tune.apply_kind == 3 || (c->tune.apply_kind == 0 && log2L == 16));
+}
 // Transforms per chunk of the two-pass apply: 8 MiB of them (256 row tasks),
 // so that the scratch (kApplyL2Slots chunks, 32 MiB) stays in L2 beside the
 // spectra and factor tables.
