@@ -82,11 +82,17 @@ DC_DEV void sinc_d012(float a, float S, float C, float& s0, float& s1, float& s2
   }
 }
 
+// Shared-memory pitch of one tap's three coefficient rows: 28 floats
+// (112 bytes), so that lanes on taps up to 8 apart read different banks
+// (at 24 floats, taps 4 apart collided).
+constexpr int kWPitch = 3 * kWCoef + 4;
+
 // Window w(e - j) and its first two derivatives in e from tap t's degree-7
 // polynomial and its derivative polynomials (t = j + 15), staged in shared
-// memory as [tap][3][8] coefficients.
+// memory as [tap][kWPitch] (value, first- and second-derivative rows of
+// kWCoef coefficients each).
 DC_DEV void window_d012(const float* wp, int t, float e, float& w0, float& w1, float& w2) {
-  const float4* q = reinterpret_cast<const float4*>(wp + t * 3 * kWCoef);
+  const float4* q = reinterpret_cast<const float4*>(wp + t * kWPitch);
   const float4 a0 = q[0], a1 = q[1], b0 = q[2], b1 = q[3], c0 = q[4], c1 = q[5];
   w0 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(a1.w, e, a1.z), e, a1.y), e, a1.x), e, a0.w), e, a0.z), e, a0.y),
             e, a0.x);
@@ -115,11 +121,11 @@ DC_DEV void split8_f16(const float (&v)[8], uint4& hi, uint4& lo) {
 __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ float2 win[kWin];
-  __shared__ __align__(16) float s_wp[32 * 3 * kWCoef];
+  __shared__ __align__(16) float s_wp[32 * kWPitch];
   __shared__ int s_m[kV], s_vidx[kV];
   __shared__ float s_e[kV], s_sin[kV], s_cos[kV], s_dl[kV];
-  __shared__ float s_max[kThreads / 32];
-  __shared__ int s_mlo, s_kk, s_exp;
+  __shared__ int s_maxbits;
+  __shared__ int s_mlo, s_kk;
   __shared__ __align__(8) unsigned long long mma_bar;
   __shared__ uint32_t tmem_base;
 
@@ -132,7 +138,8 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
   const int g0 = blockIdx.y * kV;
   const float nc = (float)n0 + 0.5f * (kTile - 1);          // tile centre (half-integer, exact)
 
-  for (int i = threadIdx.x; i < 32 * 3 * kWCoef; i += kThreads) s_wp[i] = __ldg(a.wpoly + i);
+  for (int i = threadIdx.x; i < 32 * 3 * kWCoef; i += kThreads)
+    s_wp[(i / (3 * kWCoef)) * kWPitch + i % (3 * kWCoef)] = __ldg(a.wpoly + i);
   // 1. per range rate: delta_v n_c = m_v + e_v, and the K range of the tile
   if (warp == 0) {
     const int slot = g0 + lane;
@@ -161,6 +168,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
       const int span = hi - lo;                // range-rate offsets inside the tile
       s_mlo = lo;
       s_kk = span > kKMax - 32 ? -1 : ((32 + span + 15) / 16) * 16;
+      s_maxbits = 0;
       mbar_init(&mma_bar, 1);
     }
   } else if (warp == 1) {
@@ -176,6 +184,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
   const int KK = s_kk;
   const int u0 = s_mlo - 15;                   // A column k holds x[n0 + row + u0 + k]
   bool run = KK > 0;
+  int ex = 0;                                  // the window's scale exponent
   if (!run && threadIdx.x == 0) atomicExch(a.err, 2);   // range rates spread too far
 
   if (run) {
@@ -190,21 +199,31 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) s_max[warp] = mx;
+    // non-negative floats (and +inf, NaN above them) order as their bit
+    // patterns, so the block maximum is an integer atomic max
+    if (lane == 0) atomicMax(&s_maxbits, __float_as_int(mx));
     __syncthreads();
-    if (threadIdx.x == 0) {
-      float m = 0.f;
-      for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, s_max[w]);
-      int ex = 0;
+    {
+      const float m = __int_as_float(s_maxbits);
       if (m > 0.f && isfinite(m)) frexpf(m, &ex);      // m = f 2^ex, f in [0.5, 1)
-      s_exp = ex;
     }
-    __syncthreads();
-    const float scale = ldexpf(1.f, -s_exp);
+    const float scale = ldexpf(1.f, -ex);
 
-    // 3. A: Hankel tile, 16-byte chunks of 8 columns, four planes per atom
+    // 3. A: Hankel tile, 16-byte chunks of 8 columns, four planes per atom.
+    //    A weight chunk (step 4) costs about six Hankel chunks, so the
+    //    threads without one (threadIdx.x >= chunks_b) take qa Hankel chunks
+    //    each and the others share the rest.
     const int chunks_a = kTile * (KK / 8);
-    for (int c = threadIdx.x; c < chunks_a; c += kThreads) {
+    const int chunks_b = kV * (KK / 8);        // <= kThreads
+    const int n_free = kThreads - chunks_b;
+    const int qa = n_free > 0 ? min((chunks_a + 6 * chunks_b + kThreads - 1) / kThreads,
+                                    chunks_a / n_free) : 0;
+    const int front = qa * n_free;             // chunks [0, front): the free threads
+    const bool free_t = (int)threadIdx.x >= chunks_b;
+    const int c0 = free_t ? (int)threadIdx.x - chunks_b : front + (int)threadIdx.x;
+    const int c_end = free_t ? front : chunks_a;
+    const int c_step = free_t ? n_free : chunks_b;
+    for (int c = c0; c < c_end; c += c_step) {
       const int r = c / (KK / 8), k8 = c % (KK / 8);
       const int atom = k8 >> 2, kc = k8 & 3;
       float re[8], im[8];
@@ -226,8 +245,8 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
     }
 
     // 4. B: tap weights h, h', h'' of each range rate at the tile centre;
-    //    row d * 32 + v, column k (tap j = u0 + k - m_v)
-    const int chunks_b = kV * (KK / 8);
+    //    row d * 32 + v, column k (tap j = u0 + k - m_v); one chunk per
+    //    thread below chunks_b
     for (int c = threadIdx.x; c < chunks_b; c += kThreads) {
       const int v = c % kV, k8 = c / kV;
       const int atom = k8 >> 2, kc = k8 & 3;
@@ -298,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
     const int r = 32 * q + lane;
     const int n = n0 + r;
     const float dn = (float)r - 0.5f * (kTile - 1);        // n - n_c
-    const float unscale = ldexpf(1.f, s_exp);
+    const float unscale = ldexpf(1.f, ex);
     if (ready) {
       for (int g = 0; g < 2; ++g) {
         const int vb = 16 * half + 8 * g;
