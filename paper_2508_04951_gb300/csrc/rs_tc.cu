@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
     const int c_end = free_t ? front : chunks_a;
     const int c_step = free_t ? n_free : chunks_b;
     for (int c = c0; c < c_end; c += c_step) {
-      const int r = c / (KK / 8), k8 = c % (KK / 8);
+      const int r = c % kTile, k8 = c / kTile;  // a warp: consecutive rows, one column chunk
       const int atom = k8 >> 2, kc = k8 & 3;
       float re[8], im[8];
 #pragma unroll
