@@ -1139,21 +1139,15 @@ dc_status bank_impl(dc_ctx* c, const dc_c64* x, long long n, const dc_c64* rep, 
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "phase table launch");
   }
   // 4. factors + inverse per (v_r, TEC), in chunks
-  const FftItem* dev = nullptr;
-  std::vector<FftItem> ap(n_pairs);
-  for (int i = 0; i < n_v; ++i)
-    for (int t = 0; t < n_tec; ++t) {
-      FftItem& f = ap[(size_t)i * n_tec + t];
-      f = FftItem{};
-      f.src = Sp + (size_t)i * L;
-      f.ptab = P + (size_t)t * L;
-      f.dst = reinterpret_cast<float2*>(out) + ((size_t)i * n_tec + t) * n_out;
-      f.n_valid = (int)n_out;
-      f.n_out = (int)n_out;
-    }
   if (fused) {
-    if ((st = upload(c, ap, item_at, s, &dev))) return st;
-    FusedArgs a{dev, (int)n_pairs, log2L, c->tw, c->err, c->t4};
+    // the transforms form a grid (spectrum i x factor table t): the kernels
+    // form each one from its index, no item list is uploaded
+    FusedArgs a{nullptr, (int)n_pairs, log2L, c->tw, c->err, c->t4};
+    a.grid_src = Sp;
+    a.grid_ptab = P;
+    a.grid_dst = reinterpret_cast<float2*>(out);
+    a.grid_n_tec = n_tec;
+    a.grid_n_out = (int)n_out;
     a.apply_rows2 = apply_rows2(c, log2L);
     if (l2) {
       a.scratch = reinterpret_cast<float2*>(ws + q_at);
@@ -1166,6 +1160,18 @@ dc_status bank_impl(dc_ctx* c, const dc_c64* x, long long n, const dc_c64* rep, 
     if ((e = launch_fused(FUSED_APPLY, a, s)) != cudaSuccess) return cuda_fail(c, e, "apply launch");
     return DC_OK;
   }
+  const FftItem* dev = nullptr;
+  std::vector<FftItem> ap(n_pairs);
+  for (int i = 0; i < n_v; ++i)
+    for (int t = 0; t < n_tec; ++t) {
+      FftItem& f = ap[(size_t)i * n_tec + t];
+      f = FftItem{};
+      f.src = Sp + (size_t)i * L;
+      f.ptab = P + (size_t)t * L;
+      f.dst = reinterpret_cast<float2*>(out) + ((size_t)i * n_tec + t) * n_out;
+      f.n_valid = (int)n_out;
+      f.n_out = (int)n_out;
+    }
   if (!four) {
     if ((st = upload(c, ap, item_at, s, &dev))) return st;
     RowArgs a{dev, (int)n_pairs, log2L, 0, c->tw};

@@ -213,6 +213,21 @@ template <int CL> DC_DEV void cluster_wait() {
   if constexpr (CL > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Transform p of a FUSED_APPLY launch: from the item list, or formed from
+// the grid description (FusedArgs::grid_src).
+DC_DEV FftItem apply_item(const FusedArgs& a, int p) {
+  if (!a.grid_src) return a.items[p];
+  FftItem I = {};
+  const int i = p / a.grid_n_tec, t = p - i * a.grid_n_tec;
+  const size_t L = (size_t)1 << a.log2L;
+  I.src = a.grid_src + (size_t)i * L;
+  I.ptab = a.grid_ptab + (size_t)t * L;
+  I.dst = a.grid_dst + (size_t)p * a.grid_n_out;
+  I.n_valid = a.grid_n_out;
+  I.n_out = a.grid_n_out;
+  return I;
+}
+
 // Spectra (FUSED_SPEC): one row k1 of the four-step spectrum per CTA, one
 // cluster of L1 CTAs per transform.  Each CTA runs the length-L1 forward
 // DFTs of its 4096 / L1 columns straight from global memory, applies
@@ -327,7 +342,7 @@ __global__ void __launch_bounds__(kRowThreads << LOG2G, 4 >> LOG2G) apply_kernel
   __shared__ __align__(8) unsigned long long bar_in;
 
   const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const FftItem I = a.items[blockIdx.x >> (LOG2L1 - LOG2G)];
+  const FftItem I = apply_item(a, blockIdx.x >> (LOG2L1 - LOG2G));
   const int j = threadIdx.x;
   const int h = j / kRowThreads, jj = j % kRowThreads;   // row of the CTA, thread in the row
   const int k1 = rank * G + h;
@@ -467,6 +482,19 @@ DC_DEV void wait_count(const int* p, int want, int* err) {
   atomicExch(err, 1);
 }
 
+// One task of the two-pass apply as thread 0 decodes it for the CTA.
+struct ApplyTask {
+  const float2* src;    // the transform's spectrum (row tasks)
+  const float2* ptab;   // its factor table (row tasks)
+  float2* dst;          // its output (column tasks)
+  float2* slot;         // its scratch slot
+  int n_out;
+  int p;                // transform
+  int rq;               // row k1 (row task) or column block q (column task)
+  int prev;             // the slot's previous transform, or -1
+  int kind;             // 1 row, 2 column, 0 nothing (past the last chunk), -1 queue done
+};
+
 template <int LOG2L1>
 __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
   constexpr int L1 = 1 << LOG2L1;
@@ -474,7 +502,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
   constexpr int PER = COLS / kRowThreads;       // columns per thread
   extern __shared__ __align__(128) float2 sm[]; // [kRowPitch] the row buffer
   __shared__ __align__(8) unsigned long long bar_in;
-  __shared__ int s_task[2];
+  __shared__ ApplyTask s_ti[2];                 // the task in hand and the next one
   const int j = threadIdx.x;
   const int P = a.chunk;
   const int n_chunks = (a.n_items + P - 1) / P;
@@ -486,25 +514,49 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
   int* row_done = a.ctr + 1;
   int* col_done = a.ctr + 1 + a.n_items;
   const size_t slot_elems = (size_t)L1 * kRowN;
-  int t_next = 0;                               // thread 0: the task taken ahead
-  if (j == 0) {
-    mbar_init(&bar_in, 1);
-    s_task[0] = atomicAdd(head, 1);
-  }
-  uint32_t phase = 0;
-  for (int it = 0;; ++it) {
-    __syncthreads();                            // s_task; the last task's reads of sm are done
-    const int t = s_task[it & 1];
-    if (t >= n_tasks) break;
-    if (j == 0) t_next = atomicAdd(head, 1);    // used at the end of this task
+  // thread 0 decodes each task once (the divisions stay off the other threads)
+  auto decode = [&](int t) {
+    ApplyTask d = {};
+    if (t >= n_tasks) {
+      d.kind = -1;
+      return d;
+    }
     const int b = t / per_block, w = t % per_block;
     const bool is_col = b & 1;
     const int chunk = is_col ? (b >> 1) - kApplyLag : b >> 1;
-    const int p = chunk * P + w / L1;
-    const int rq = w % L1;                      // row k1, or column block q
-    if (chunk >= 0 && chunk < n_chunks && p < a.n_items) {
-      const FftItem I = a.items[p];
-      float2* slot = a.scratch + (size_t)(p % n_slots) * slot_elems;
+    d.p = chunk * P + w / L1;
+    d.rq = w % L1;                              // row k1, or column block q
+    if (chunk < 0 || chunk >= n_chunks || d.p >= a.n_items) return d;   // kind 0: nothing
+    d.kind = is_col ? 2 : 1;
+    const FftItem I = apply_item(a, d.p);
+    d.src = I.src;
+    d.ptab = I.ptab;
+    d.dst = I.dst;
+    d.n_out = I.n_out;
+    d.slot = a.scratch + (size_t)(d.p % n_slots) * slot_elems;
+    d.prev = d.p >= n_slots ? d.p - n_slots : -1;
+    return d;
+  };
+  int t_next = 0;                               // thread 0: the task taken ahead
+  if (j == 0) {
+    mbar_init(&bar_in, 1);
+    s_ti[0] = decode(atomicAdd(head, 1));
+  }
+  uint32_t phase = 0;
+  for (int it = 0;; ++it) {
+    __syncthreads();                            // s_ti; the last task's reads of sm are done
+    const ApplyTask T = s_ti[it & 1];
+    if (T.kind < 0) break;
+    if (j == 0) t_next = atomicAdd(head, 1);    // decoded at the end of this task
+    const int p = T.p, rq = T.rq;
+    if (T.kind > 0) {
+      const bool is_col = T.kind == 2;
+      float2* slot = T.slot;
+      FftItem I = {};
+      I.src = T.src;
+      I.ptab = T.ptab;
+      I.dst = T.dst;
+      I.n_out = T.n_out;
       if (!is_col) {
         if (j == 0) {                           // the spectrum row first: its copy overlaps the rest
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // after the last generic reads
@@ -521,7 +573,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
         for (int r = 0; r < 16; ++r) v[r] = cmul(sm[j + 256 * r], v[r]);
         // the slot is free; the CTA barrier orders thread 0's wait before
         // every thread's stores (the others wait there, polling nothing)
-        if (j == 0 && p >= n_slots) wait_count(col_done + p - n_slots, L1, a.err);
+        if (j == 0 && T.prev >= 0) wait_count(col_done + T.prev, L1, a.err);
         __syncthreads();                        // also: the row FFT overwrites sm
         row4096_1buf<+1>(v, sm, j, a.tw);       // v[r] = Y[j + 256 r]
         float2* yrow = slot + (size_t)rq * kRowN;
@@ -532,13 +584,13 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
       } else {
         if (j == 0) wait_count(row_done + p, L1, a.err);
         __syncthreads();
-        const float2* T = a.t4 + kT4Offset(L1);
+        const float2* tw4 = a.t4 + kT4Offset(L1);
 #pragma unroll
         for (int pp = 0; pp < PER; ++pp) {
           const int n2 = rq * COLS + j + 256 * pp;
           float2 w4[4];
 #pragma unroll
-          for (int bb = 0; bb < LOG2L1; ++bb) w4[bb] = __ldg(T + bb * kRowN + n2);   // W_L^(-2^b n2)
+          for (int bb = 0; bb < LOG2L1; ++bb) w4[bb] = __ldg(tw4 + bb * kRowN + n2);   // W_L^(-2^b n2)
           float2 col[L1];
 #pragma unroll
           for (int q = 0; q < L1; ++q) col[q] = __ldcg(slot + (size_t)q * kRowN + n2);
@@ -554,7 +606,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
         if (j == 0) red_release_gpu(col_done + p, 1);   // every thread's slot reads first
       }
     }
-    if (j == 0) s_task[(it + 1) & 1] = t_next;
+    if (j == 0) s_ti[(it + 1) & 1] = decode(t_next);
   }
 }
 

@@ -50,6 +50,15 @@ struct FusedArgs {
   float2* scratch;
   int* ctr;
   int chunk;
+  // FUSED_APPLY over a grid of transforms (the bank): with grid_src set,
+  // transform p = i * grid_n_tec + t reads the spectrum grid_src + i L and
+  // the factors grid_ptab + t L and writes grid_n_out samples to
+  // grid_dst + p grid_n_out; `items` is not read.
+  const float2* grid_src;
+  const float2* grid_ptab;
+  float2* grid_dst;
+  int grid_n_tec;
+  int grid_n_out;
 };
 
 // Four-step twiddle rows for L1 = 2, 4, 8, 16: log2(L1) rows of 4096 per L1.
