@@ -582,19 +582,21 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
         __syncthreads();
         if (j == 0) red_release_gpu(row_done + p, 1);   // every thread's row stores first
       } else {
+        const float2* tw4 = a.t4 + kT4Offset(L1);
+        float2 w4[PER][4];                      // W_L^(-2^b n2), loaded ahead of the wait
+#pragma unroll
+        for (int pp = 0; pp < PER; ++pp)
+#pragma unroll
+          for (int bb = 0; bb < LOG2L1; ++bb) w4[pp][bb] = __ldg(tw4 + bb * kRowN + rq * COLS + j + 256 * pp);
         if (j == 0) wait_count(row_done + p, L1, a.err);
         __syncthreads();
-        const float2* tw4 = a.t4 + kT4Offset(L1);
 #pragma unroll
         for (int pp = 0; pp < PER; ++pp) {
           const int n2 = rq * COLS + j + 256 * pp;
-          float2 w4[4];
-#pragma unroll
-          for (int bb = 0; bb < LOG2L1; ++bb) w4[bb] = __ldg(tw4 + bb * kRowN + n2);   // W_L^(-2^b n2)
           float2 col[L1];
 #pragma unroll
           for (int q = 0; q < L1; ++q) col[q] = __ldcg(slot + (size_t)q * kRowN + n2);
-          apply_powers<L1>(col, w4);
+          apply_powers<L1>(col, w4[pp]);
           dft<L1, +1>(col);
 #pragma unroll
           for (int n1 = 0; n1 < L1; ++n1) {
