@@ -63,9 +63,9 @@ UNIT = "Msamples/s"
 ALGO_BYTES_PER_SAMPLE = 8        # one complex64 corrected sample written
 # DRAM bytes (read + write) per launch of the kernel at the full workload, from
 # one ncu capture of the full-size launch (the two-pass apply kernel:
-# dram__bytes_read.sum 176,610,304 + dram__bytes_write.sum 2,208,197,888).
+# dram__bytes_read.sum 175,613,696 + dram__bytes_write.sum 2,206,697,216).
 # Cleared whenever the kernel changes after the capture.
-TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 176610304.0 + 2208197888.0}
+TRAFFIC_PER_LAUNCH: dict[str, float | None] = {"fused_apply": 175613696.0 + 2206697216.0}
 
 
 def load_peaks() -> tuple[float, str]:
