@@ -192,67 +192,67 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   __shared__ __align__(16) float2 win[NW * WSTRIDE];
   __shared__ float4 wts[NW][TAPS];
   __shared__ __align__(8) unsigned long long mbar;
-  __shared__ int s_item;
+  __shared__ int s_geo[6];                     // item, wlo, t0, t1, sh, window too long
+  __shared__ int s_done;
 
+  // Warp 0 finds the tile's item; its lane 0 sets out the CTA's input window
+  // and starts the TMA copy, alone (nothing in this is needed twice).
   const int tile = blockIdx.x;
   if (threadIdx.x < 32) {
     const int it = find_item(a, tile);
-    if (threadIdx.x == 0) s_item = it;
+    if (threadIdx.x == 0) {
+      const RsItem& J = a.items[it];
+      const int p0 = (tile - J.tile_begin) * kRsTile;
+      int flA, flB;
+      float eA, eB;
+      rs_delay(J.dl_hi, J.dl_lo, (float)p0, flA, eA);
+      rs_delay(J.dl_hi, J.dl_lo, (float)(p0 + kRsTile - 1), flB, eB);
+      const int flmin = min(flA, flB) - 2, flmax = max(flA, flB) + 2;
+      const int lo = p0 + flmin - HALF + 1;
+      const int hi = p0 + kRsTile - 1 + flmax + HALF;
+      const bool too_long = hi - lo + 1 > WINMAX;   // |delta| outside the tiled range
+      // the 16-byte-aligned interior of the valid part, by one bulk copy
+      const int vlo = max(lo, 0), vhi = min(hi, J.n_in - 1);
+      int u0 = vlo, u1 = vhi + 1;
+      if (u1 > u0 && (reinterpret_cast<uintptr_t>(J.x + u0) & 15)) ++u0;
+      if (u1 > u0 && ((u1 - u0) & 1)) --u1;
+      if (u1 < u0) u1 = u0;
+      const int shift = (u0 - lo) & 1;
+      s_geo[0] = it;
+      s_geo[1] = lo;
+      s_geo[2] = u0;
+      s_geo[3] = u1;
+      s_geo[4] = shift;
+      s_geo[5] = too_long;
+      const uint32_t bytes = (uint32_t)(u1 - u0) * 8u;
+      if (!too_long && bytes) {
+        const uint32_t mb = smem_u32(&mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(stage + (u0 - lo + shift))),
+            "l"(J.x + u0), "r"(bytes), "r"(mb)
+            : "memory");
+      }
+    }
   }
   __syncthreads();
-  const RsItem& I = a.items[s_item];
+  const RsItem& I = a.items[s_geo[0]];
   const int o0 = (tile - I.tile_begin) * kRsTile;
-
-  // Input window of the CTA's kRsTile outputs.
-  int flA, flB;
-  float eA, eB;
-  rs_delay(I.dl_hi, I.dl_lo, (float)o0, flA, eA);
-  rs_delay(I.dl_hi, I.dl_lo, (float)(o0 + kRsTile - 1), flB, eB);
-  const int flmin = min(flA, flB) - 2, flmax = max(flA, flB) + 2;
-  const int wlo = o0 + flmin - HALF + 1;
-  const int whi = o0 + kRsTile - 1 + flmax + HALF;
-  const int wlen = whi - wlo + 1;
-  if (wlen > WINMAX) {                       // |delta| outside the tiled range
+  const int wlo = s_geo[1], t0 = s_geo[2], t1 = s_geo[3], sh = s_geo[4];
+  if (s_geo[5]) {
     if (threadIdx.x == 0) atomicExch(a.err, 2);
     return;
   }
-
-  // TMA bulk copy of the 16-byte-aligned interior of the valid part.
-  const int vlo = max(wlo, 0), vhi = min(whi, I.n_in - 1);
-  int t0 = vlo, t1 = vhi + 1;
-  if (t1 > t0 && (reinterpret_cast<uintptr_t>(I.x + t0) & 15)) ++t0;
-  if (t1 > t0 && ((t1 - t0) & 1)) --t1;
-  if (t1 < t0) t1 = t0;
-  const int sh = (t0 - wlo) & 1;
-  const uint32_t bytes = (uint32_t)(t1 - t0) * 8u;
-  if (bytes) {
-    const uint32_t mb = smem_u32(&mbar);
+  if (t1 > t0) {
+    // thread 0 waits for the copy (bounded); the others wait at the barrier
     if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
-                   : "memory");
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              smem_u32(stage + (t0 - wlo + sh))),
-          "l"(I.x + t0), "r"(bytes), "r"(mb)
-          : "memory");
-    }
-    uint32_t done = 0;
-    for (int it = 0; it < kWaitLimit && !done; ++it) {
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(done)
-          : "r"(mb)
-          : "memory");
-    }
-    if (!__syncthreads_and(done)) {            // every thread takes the same exit
-      if (threadIdx.x == 0) atomicExch(a.err, 1);
-      done = 0;
+      const uint32_t mb = smem_u32(&mbar);
+      uint32_t done = 0;
       for (int it = 0; it < kWaitLimit && !done; ++it) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
@@ -260,8 +260,20 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
             : "r"(mb)
             : "memory");
       }
-      return;
+      if (!done) {
+        atomicExch(a.err, 1);
+        for (int it = 0; it < kWaitLimit && !done; ++it) {   // the copy must land before the exit
+          asm volatile(
+              "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+              : "=r"(done)
+              : "r"(mb)
+              : "memory");
+        }
+      }
+      s_done = done;
     }
+    __syncthreads();
+    if (!s_done) return;
   }
   // Each warp repacks its own slice of the window -- global positions
   // G .. G + WWIN - 1, G = ow + min(f0, f2) - HALF + 1 -- into a private,
@@ -271,11 +283,16 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   const int ow = o0 + warp * W;
   if (ow >= I.n_out) return;                   // warp-uniform: nothing to write
   constexpr float H = 0.5f * (W - 1);
-  int f0, f1, f2;
-  float e0, e1, e2;
-  rs_delay(I.dl_hi, I.dl_lo, (float)ow, f0, e0);
-  rs_delay(I.dl_hi, I.dl_lo, (float)ow + H, f1, e1);
-  rs_delay(I.dl_hi, I.dl_lo, (float)(ow + W - 1), f2, e2);
+  // the warp tile's first, centre and last positions: one per lane 0..2
+  int fl_l;
+  float e_l;
+  rs_delay(I.dl_hi, I.dl_lo, lane == 0 ? (float)ow : lane == 1 ? (float)ow + H : (float)(ow + W - 1),
+           fl_l, e_l);
+  const float s_l = sinpif(e_l) * kInvPi;
+  const int f0 = __shfl_sync(0xffffffffu, fl_l, 0), f1 = __shfl_sync(0xffffffffu, fl_l, 1),
+            f2 = __shfl_sync(0xffffffffu, fl_l, 2);
+  const float e0 = __shfl_sync(0xffffffffu, e_l, 0), e1 = __shfl_sync(0xffffffffu, e_l, 1),
+              e2 = __shfl_sync(0xffffffffu, e_l, 2);
   if (abs(f2 - f0) > 4) {                      // |delta| too large for the slice
     if (lane == 0) atomicExch(a.err, 2);
     return;
@@ -297,7 +314,8 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   for (int q = 0; q < Q; ++q) acc[q] = make_float2(0.f, 0.f);
   if (f0 == f2 && f0 == f1 && fabsf(e2 - e0) <= kQuadSpan) {
     // Quadratic weights per tap through the three nodes s = -H, 0, +H.
-    const float s0 = sinpif(e0) * kInvPi, s1 = sinpif(e1) * kInvPi, s2 = sinpif(e2) * kInvPi;
+    const float s0 = __shfl_sync(0xffffffffu, s_l, 0), s1 = __shfl_sync(0xffffffffu, s_l, 1),
+                s2 = __shfl_sync(0xffffffffu, s_l, 2);
     for (int t = lane; t < TAPS; t += 32) {
       const int k = t - HALF + 1;
       const float hA = tap_weight(a, e0, s0, k);
