@@ -119,7 +119,9 @@ DC_API const char* dc_last_error(const dc_ctx* ctx);
 /* Synchronise `stream`, then report and clear the context's device-side
  * error flag: DC_ETIMEOUT if a bounded wait inside a kernel ran out,
  * DC_EINVAL if a kernel met parameters outside its range, DC_ECUDA on an
- * asynchronous CUDA error. */
+ * asynchronous CUDA error or, in the checked build (libdc compiled with
+ * DC_CHECKED: bounds checks in the kernels, a failed one skips its access),
+ * on a failed bounds check. */
 DC_API dc_status dc_check(dc_ctx* ctx, void* stream);
 
 /* Failure-detection self-test: queues on `stream` one kernel that waits, with

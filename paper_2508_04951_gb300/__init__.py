@@ -77,7 +77,8 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """libdc.so, or its checked build when the environment sets DC_CHECKED=1."""
+    return _build.LIB_CHECKED if os.environ.get("DC_CHECKED") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = False) -> ctypes.CDLL:
@@ -91,7 +92,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             raise RuntimeError(
                 f"CUDA library {path} is not built; run paper_2508_04951_gb300.build.build() "
                 "(or __graft_entry__.build()) first")
-        _build.build()
+        _build.build(checked=path == _build.LIB_CHECKED)
     lib = ctypes.CDLL(path)
     vp, ll, d, i = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double, ctypes.c_int
     dp = ctypes.POINTER(ctypes.c_double)

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dc.h"
 #include "exact_tc.cuh"
 #include "fft.cuh"
@@ -160,6 +162,7 @@ struct Phase {
   Phase(dc_ctx* c_, int id_, cudaStream_t s_, long long samples_)
       : c(c_), id(id_), s(s_), samples(samples_) {
     ++c->launches;
+    nvtxRangePushA(kPhaseName[id]);   // host-side range per phase (profilers; no cost without one)
     if (c->profiling && !c->rec) {
       a = take_event(c);
       cudaEventRecord(a, s);
@@ -171,6 +174,7 @@ struct Phase {
       cudaEventRecord(b, s);
       c->pending.push_back({id, a, b, samples});
     }
+    nvtxRangePop();
   }
 };
 
@@ -776,6 +780,7 @@ dc_status dc_check(dc_ctx* c, void* stream) {
   if (flag) {
     cudaMemset(c->err, 0, sizeof(int));
     if (flag == 1) return fail(c, DC_ETIMEOUT, "a kernel's bounded wait ran out");
+    if (flag == 3) return fail(c, DC_ECUDA, "a bounds check of the checked build failed");
     return fail(c, DC_EINVAL, "a kernel met parameters outside its range (code %d)", flag);
   }
   return DC_OK;
@@ -952,7 +957,7 @@ __global__ void stuck_wait_kernel(int* err, int polls) {
   mbar_init(&bar, 1);
   for (int i = 0; i < polls; ++i)
     if (mbar_try_wait(&bar, 0)) return;
-  atomicExch(err, 1);
+  atomicMax(err, 1);
 }
 
 // Factor tables P[t][.] in the spectrum layout (element k1*4096 + k2 holds

@@ -182,6 +182,19 @@ template <int R, int DIR> DC_DEV void dft(float2 (&v)[R]) {
   }
 }
 
+// Bounds checks of the checked build (compiled with -DDC_CHECKED).  A failed
+// check raises the context's error flag to 3 (flags only rise: 3 bounds, 2
+// parameters out of range, 1 a bounded wait ran out) and the caller skips the
+// access -- never a trap.  In the normal build every check is `true`.
+DC_DEV void bounds_fail(int* err) {
+  if (err) atomicMax(err, 3);
+}
+#ifdef DC_CHECKED
+#define DC_IN_BOUNDS(cond, err) ((cond) ? true : (::dc::bounds_fail(err), false))
+#else
+#define DC_IN_BOUNDS(cond, err) true
+#endif
+
 // v[q] *= w^q for q = 1 .. N-1 (N = 2, 4, 8, 16) from correctly rounded
 // b[0] = w, b[1] = w^2, b[2] = w^4, b[3] = w^8 (entries past log2 N unused):
 // w^q is the product of the bases of q's set bits, so every factor carries

@@ -243,8 +243,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint4 hi, lo;
         split8<FP16>(v, hi, lo);
         const int off = r * 64 + ((k8 ^ ((r >> 1) & 3)) << 4);
-        *reinterpret_cast<uint4*>(st + h * kAPlane + off) = hi;
-        *reinterpret_cast<uint4*>(st + (C::MH + h) * kAPlane + off) = lo;
+        if (DC_IN_BOUNDS((C::MH + h) * kAPlane + off + 16 <= C::A_BYTES && off + 16 <= kAPlane, a.err)) {
+          *reinterpret_cast<uint4*>(st + h * kAPlane + off) = hi;
+          *reinterpret_cast<uint4*>(st + (C::MH + h) * kAPlane + off) = lo;
+        }
       }
       async_proxy_fence();                     // our generic-proxy writes -> async proxy
       __syncwarp();

@@ -378,11 +378,14 @@ __global__ void __launch_bounds__(kRowThreads << LOG2G, 4 >> LOG2G) apply_kernel
     // is inside the row FFT)
     cluster_wait<L1>();
     const uint32_t r_loc = smem_addr(R + k1 * PCOLS + sw16(jj));   // rpos(hw_sigma(jj))
+    // the farthest element this thread writes in its owners' buffers
+    if (DC_IN_BOUNDS(k1 * PCOLS + sw16(jj) + 256 * (PER - 1) < L1 * PCOLS && 16 / PER <= CL, a.err)) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int owner = r / PER;                // n2 = hw_sigma(jj) + 256 r -> owner n2 / COLS
-      const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));   // rpos(c + 256 m)
-      st_cluster_c64(dsmem_map(r_loc + off, owner), v[r]);
+      for (int r = 0; r < 16; ++r) {
+        const int owner = r / PER;              // n2 = hw_sigma(jj) + 256 r -> owner n2 / COLS
+        const uint32_t off = (uint32_t)(256 * (r % PER) * sizeof(float2));   // rpos(c + 256 m)
+        st_cluster_c64(dsmem_map(r_loc + off, owner), v[r]);
+      }
     }
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");   // rows delivered
     const float2* T = a.t4 + kT4Offset(L1);
@@ -479,7 +482,7 @@ DC_DEV void wait_count(const int* p, int want, int* err) {
     if (ld_acquire_gpu(p) >= want) return;
     __nanosleep(64);
   }
-  atomicExch(err, 1);
+  atomicMax(err, 1);
 }
 
 // One task of the two-pass apply as thread 0 decodes it for the CTA.
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
     if (T.kind < 0) break;
     if (j == 0) t_next = atomicAdd(head, 1);    // decoded at the end of this task
     const int p = T.p, rq = T.rq;
-    if (T.kind > 0) {
+    if (T.kind > 0 && DC_IN_BOUNDS(rq >= 0 && rq < L1 && p >= 0 && p < a.n_items, a.err)) {
       const bool is_col = T.kind == 2;
       float2* slot = T.slot;
       FftItem I = {};

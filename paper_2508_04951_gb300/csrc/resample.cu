@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   const int o0 = (tile - I.tile_begin) * kRsTile;
   const int wlo = s_geo[1], t0 = s_geo[2], t1 = s_geo[3], sh = s_geo[4];
   if (s_geo[5]) {
-    if (threadIdx.x == 0) atomicExch(a.err, 2);
+    if (threadIdx.x == 0) atomicMax(a.err, 2);
     return;
   }
   if (t1 > t0) {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
             : "memory");
       }
       if (!done) {
-        atomicExch(a.err, 1);
+        atomicMax(a.err, 1);
         for (int it = 0; it < kWaitLimit && !done; ++it) {   // the copy must land before the exit
           asm volatile(
               "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   const float e0 = __shfl_sync(0xffffffffu, e_l, 0), e1 = __shfl_sync(0xffffffffu, e_l, 1),
               e2 = __shfl_sync(0xffffffffu, e_l, 2);
   if (abs(f2 - f0) > 4) {                      // |delta| too large for the slice
-    if (lane == 0) atomicExch(a.err, 2);
+    if (lane == 0) atomicMax(a.err, 2);
     return;
   }
   const int fmin = min(f0, f2);
@@ -303,9 +303,12 @@ __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a)
   for (int i = lane; i < WWIN; i += 32) {
     const int gi = G + i;
     float2 v = make_float2(0.f, 0.f);
-    if (gi >= t0 && gi < t1) v = stage[gi - wlo + sh];
-    else if (gi >= 0 && gi < I.n_in) v = __ldg(I.x + gi);
-    ww[wpad<LQ>(i)] = v;
+    if (gi >= t0 && gi < t1) {
+      if (DC_IN_BOUNDS(gi - wlo + sh >= 0 && gi - wlo + sh < WINMAX + 2, a.err)) v = stage[gi - wlo + sh];
+    } else if (gi >= 0 && gi < I.n_in) {
+      v = __ldg(I.x + gi);
+    }
+    if (DC_IN_BOUNDS(wpad<LQ>(i) < WSTRIDE, a.err)) ww[wpad<LQ>(i)] = v;
   }
   __syncwarp();
 

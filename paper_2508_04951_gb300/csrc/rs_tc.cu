@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
   const int u0 = s_mlo - 15;                   // A column k holds x[n0 + row + u0 + k]
   bool run = KK > 0;
   int ex = 0;                                  // the window's scale exponent
-  if (!run && threadIdx.x == 0) atomicExch(a.err, 2);   // range rates spread too far
+  if (!run && threadIdx.x == 0) atomicMax(a.err, 2);   // range rates spread too far
 
   if (run) {
     // 2. input window x[n0 + u0 .. + kTile + KK - 1] (zero outside the pulse)
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
     for (int i = threadIdx.x; i < kTile + KK; i += kThreads) {
       const int gi = n0 + u0 + i;
       const float2 v = (gi >= 0 && gi < a.n_in) ? __ldg(a.x + gi) : make_float2(0.f, 0.f);
-      win[i] = v;
+      if (DC_IN_BOUNDS(i < kWin, a.err)) win[i] = v;
       mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
 #pragma unroll
@@ -226,6 +226,9 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
     for (int c = c0; c < c_end; c += c_step) {
       const int r = c % kTile, k8 = c / kTile;  // a warp: consecutive rows, one column chunk
       const int atom = k8 >> 2, kc = k8 & 3;
+      if (!DC_IN_BOUNDS(atom * 4 * kAPlane + 3 * kAPlane + sw64_offset(r, kc) + 16 <= kA &&
+                            r + 8 * k8 + 8 <= kWin, a.err))
+        continue;
       float re[8], im[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -273,6 +276,8 @@ __global__ void __launch_bounds__(kThreads, 2) rs_tc_kernel(RsTcArgs a) {
         w[2][i] = h2;
       }
       uint8_t* bt = B + atom * 2 * kBPlane;
+      if (!DC_IN_BOUNDS(atom * 2 * kBPlane + kBPlane + sw64_offset(2 * kV + v, kc) + 16 <= kB, a.err))
+        continue;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         uint4 hi, lo;

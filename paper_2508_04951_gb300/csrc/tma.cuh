@@ -49,7 +49,7 @@ DC_DEV bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
 DC_DEV bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, int* err) {
   for (int i = 0; i < kMbarPollLimit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicExch(err, 1);
+  if (err) atomicMax(err, 1);
   for (int i = 0; i < kMbarPollLimit; ++i)
     if (mbar_try_wait(bar, parity)) return false;
   return false;
@@ -95,7 +95,7 @@ DC_DEV bool mbar_try_wait_cluster(unsigned long long* bar, uint32_t parity) {
 DC_DEV bool mbar_wait_cluster_bounded(unsigned long long* bar, uint32_t parity, int* err) {
   for (int i = 0; i < kMbarPollLimit; ++i)
     if (mbar_try_wait_cluster(bar, parity)) return true;
-  if (err) atomicExch(err, 1);
+  if (err) atomicMax(err, 1);
   for (int i = 0; i < kMbarPollLimit; ++i)
     if (mbar_try_wait_cluster(bar, parity)) return false;
   return false;
