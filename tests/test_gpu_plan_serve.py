@@ -166,3 +166,18 @@ def test_serve_budget_too_small_for_a_full_pulse(dcg):
     with pytest.raises(dcg.DcError) as e:
         dcg.dc_serve_start(0, 16 << 20, slots=2)
     assert e.value.status == 1
+
+
+def test_serve_budget_beyond_the_device_is_enomem_and_the_device_survives(dcg, ctx):
+    # a budget far beyond the GPU's memory: the pool allocation fails cleanly
+    # (DC_ENOMEM, nothing launched), and the device keeps working
+    import torch
+    with pytest.raises(dcg.DcError) as e:
+        dcg.dc_serve_start(0, 1 << 50, slots=2)
+    assert e.value.status == 2                       # DC_ENOMEM
+    x = synth.bandlimited_noise(4096, synth.rng_for(8, salt=1)).astype(np.complex64)
+    y = torch.empty(4096, dtype=torch.complex64, device="cuda")
+    dcg.iono_correct(ctx, torch.from_numpy(x).cuda(), y, 20e6, 1e9, 40.0)
+    dcg.dc_check(ctx)
+    ref = oracle.iono_correct(x.astype(np.complex128), 20e6, 1e9, 40.0)
+    assert np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5
