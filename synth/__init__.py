@@ -37,6 +37,14 @@ def lfm(n: int, fs: float, bandwidth: float) -> np.ndarray:
     return np.exp(1j * np.pi * k * (t - T / 2.0) ** 2)
 
 
+def rf_lfm(n: int, fs: float, f0: float, bandwidth: float, T: float) -> np.ndarray:
+    """Complex RF samples of an LFM of duration T centred at f0: the phase
+    2 pi (f0 - B/2) t + pi (B/T) t^2 at t = i / fs, i < n (the sweep f0 - B/2
+    .. f0 + B/2 over T; past T the formula extends)."""
+    t = np.arange(n, dtype=np.float64) / fs
+    return np.exp(1j * (2 * np.pi * (f0 - bandwidth / 2) * t + np.pi * (bandwidth / T) * t * t))
+
+
 def bandlimited_noise(n: int, rng: np.random.Generator, frac: float = 0.8) -> np.ndarray:
     """Unit-variance complex Gaussian noise low-passed to |f| <= frac * fs/2:
     draw CN(0,1) samples, zero the DFT bins above the cut-off, transform back
