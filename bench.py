@@ -1088,6 +1088,9 @@ def run_paper_pulse(args) -> dict:
     return {
         "metric": METRIC, "value": io["gsamples_per_s"] * 1e3, "unit": UNIT, "n_gpus": 1,
         "steps": R, "warmup": 5, "ms_per_step": io["device_us"]["p50"] / 1e3, "higher_is_better": True,
+        # the paper's own figure for this workload: 2^19 samples in about 46 us,
+        # about 11.3 G samples/s, on one H100 (other hardware: context)
+        "vs_baseline": io["gsamples_per_s"] * 1e3 / 11300.0,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "paper_single_pulse", "n": L, "fs_hz": fs, "f0_hz": f0, "bandwidth_hz": B,
                    "T_s": T, "tec_tecu": tec, "v_r": v_r, "l2": "4 MiB pulse: L2-resident (latency workload)"},
