@@ -349,12 +349,17 @@ DC_API dc_status dc_plan_destroy(dc_plan* plan);
  * batches in flight return memory (admission by the HBM budget), one that
  * finds every slot busy waits for a slot.  A slot's batch runs H2D ->
  * correct_batch -> D2H on its stream while the next slot fills with requests
- * that arrived meanwhile.  Results do not depend on the batch a request rode
- * in.
+ * that arrived meanwhile.  Where the device reads and writes pageable host
+ * memory through the host's page tables (GB300 with its Grace host), H2D and
+ * D2H are copy kernels between the callers' buffers and the pool, with no
+ * host copies; elsewhere, or with the environment variable DC_SERVE_STAGED=1
+ * at dc_serve_start, host threads copy through the slot's pinned staging.
+ * Results do not depend on the batch a request rode in.
  *
- * dc_serve_submit queues one pulse (x_host: [n] samples, read when the request
+ * dc_serve_submit queues one pulse (x_host: [n] samples, read after the request
  * is admitted; y_host: [n] corrected samples, written before dc_serve_wait
- * returns DC_OK; both must stay valid until then).  n <= 2^20.  Writes the
+ * returns DC_OK; both must stay valid and untouched by the caller until
+ * then).  n <= 2^20.  Writes the
  * request id.  dc_serve_wait blocks up to timeout_ms (< 0: forever) for a
  * request (DC_ETIMEOUT if still running; the request stays valid), writes its
  * latency from submission to completion, and forgets it.  dc_serve_cancel

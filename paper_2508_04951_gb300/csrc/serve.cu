@@ -14,13 +14,20 @@
 // scheduler does not wait for the GPU, so the next slot fills with requests
 // that arrive meanwhile and batches overlap on the device.  Completed slots
 // (event query) hand results back to the callers' buffers, return their pool
-// block and record the latency from submission to completion.  Each
+// block and record the latency from submission to completion.  Where the
+// device reads and writes pageable host memory through the host's page tables
+// (GB300 with its Grace host), the batch's inputs and outputs move between
+// the callers' buffers and the pool by copy kernels on the slot's stream
+// (gather before correct_batch, scatter after it): no host copies, no
+// staging, nothing on the scheduler thread; elsewhere (or with
+// DC_SERVE_STAGED=1) host threads copy through pinned staging.  Each
 // request's result does not depend on which batch it rode in (correct_batch's
 // per-item independence).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -54,11 +61,13 @@ struct Slot {
   cudaEvent_t done = nullptr;
   dc_c64* in_host = nullptr;    // pinned
   dc_c64* out_host = nullptr;   // pinned
+  struct CopyChunk* chunks = nullptr;   // pinned: the gather / scatter lists (direct mode)
   long long cap = 0;            // samples of staging
   size_t block = 0, block_bytes = 0;   // this batch's pool block (offset, bytes)
   std::vector<Request*> reqs;
   std::vector<long long> offs;
   bool busy = false;
+  bool direct_batch = false;    // this batch moves its data by copy kernels
 };
 
 // First-fit allocator over the device pool (offsets; 256-byte granules).
@@ -191,6 +200,7 @@ class CopyPool {
 
 struct dc_server {
   int device = 0;
+  bool direct = false;          // gather / scatter kernels on the callers' buffers
   dc_opts opts{};
   std::vector<Slot> slots;
   long long cap = 0;            // samples per batch (staging)
@@ -214,13 +224,53 @@ struct dc_server {
 
 namespace {
 
+// One chunk of a gather or scatter: n samples from src to dst (one side a
+// caller's host buffer, read or written by the device through the host's page
+// tables; the other the batch's block of the device pool).
+struct CopyChunk {
+  const dc_c64* src;
+  dc_c64* dst;
+  long long n;
+};
+constexpr int kCopyChunk = 16384;              // samples per chunk (one CTA)
+constexpr int kMaxChunks = 65536;              // per slot and list (gather, scatter)
+
+__global__ void __launch_bounds__(256) copy_chunks_kernel(const CopyChunk* __restrict__ list) {
+  const CopyChunk c = list[blockIdx.x];
+  const bool v4 = ((reinterpret_cast<uintptr_t>(c.src) | reinterpret_cast<uintptr_t>(c.dst)) & 15) == 0;
+  if (v4) {
+    const float4* s4 = reinterpret_cast<const float4*>(c.src);
+    float4* d4 = reinterpret_cast<float4*>(c.dst);
+    for (long long i = threadIdx.x; i < c.n / 2; i += blockDim.x) d4[i] = s4[i];
+    if ((c.n & 1) && threadIdx.x == 0) c.dst[c.n - 1] = c.src[c.n - 1];
+  } else {
+    for (long long i = threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = c.src[i];
+  }
+}
+
+// The chunk list of a batch's gather (to_dev) or scatter into `list`;
+// returns the number of chunks, or -1 when more than kMaxChunks are needed.
+int chunk_list(const Slot& sl, dc_c64* dev, bool to_dev, CopyChunk* list) {
+  int k = 0;
+  for (size_t i = 0; i < sl.reqs.size(); ++i) {
+    const Request* r = sl.reqs[i];
+    for (long long o = 0; o < r->n; o += kCopyChunk) {
+      if (k == kMaxChunks) return -1;
+      const long long m = std::min<long long>(kCopyChunk, r->n - o);
+      dc_c64* d = dev + sl.offs[i] + o;
+      list[k++] = to_dev ? CopyChunk{r->x + o, d, m} : CopyChunk{d, r->y + o, m};
+    }
+  }
+  return k;
+}
+
 // Hand a completed slot's results back (called with the lock held; drops it
 // while copying: the slot's requests are in flight, which waiters and cancel
 // leave alone).
 void finish_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
   const cudaError_t e = cudaEventQuery(sl.done);
   lk.unlock();
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && !sl.direct_batch) {   // direct batches wrote the callers' buffers already
     std::vector<CopyPool::Job> jobs;
     for (size_t i = 0; i < sl.reqs.size(); ++i)
       jobs.push_back({sl.reqs[i]->y, sl.out_host + sl.offs[i], (size_t)sl.reqs[i]->n * sizeof(dc_c64)});
@@ -297,24 +347,41 @@ bool launch_slot(dc_server* s, Slot& sl, std::unique_lock<std::mutex>& lk) {
   sl.block_bytes = bytes;
   sl.busy = true;
   lk.unlock();
-  std::vector<CopyPool::Job> jobs;
-  for (size_t i = 0; i < sl.reqs.size(); ++i)
-    jobs.push_back({sl.in_host + sl.offs[i], sl.reqs[i]->x, (size_t)sl.reqs[i]->n * sizeof(dc_c64)});
-  s->copies->run(jobs);
   char* base = s->pool + sl.block;
   const size_t io = PoolAlloc::round((size_t)used * sizeof(dc_c64));
   dc_c64* in_dev = reinterpret_cast<dc_c64*>(base);
   dc_c64* out_dev = reinterpret_cast<dc_c64*>(base + io);
   dc_status st = DC_OK;
-  if (cudaMemcpyAsync(in_dev, sl.in_host, (size_t)used * sizeof(dc_c64), cudaMemcpyHostToDevice,
-                      sl.stream) != cudaSuccess)
-    st = DC_ECUDA;
+  // direct: the gather and scatter lists (the slot's previous batch has
+  // completed, so its lists are free)
+  int n_in = -1, n_out = -1;
+  if (s->direct) {
+    n_in = chunk_list(sl, in_dev, true, sl.chunks);
+    if (n_in >= 0) n_out = chunk_list(sl, out_dev, false, sl.chunks + kMaxChunks);
+  }
+  sl.direct_batch = n_in >= 0 && n_out >= 0;
+  if (sl.direct_batch) {
+    if (n_in > 0) copy_chunks_kernel<<<n_in, 256, 0, sl.stream>>>(sl.chunks);
+    if (cudaGetLastError() != cudaSuccess) st = DC_ECUDA;
+  } else {
+    std::vector<CopyPool::Job> jobs;
+    for (size_t i = 0; i < sl.reqs.size(); ++i)
+      jobs.push_back({sl.in_host + sl.offs[i], sl.reqs[i]->x, (size_t)sl.reqs[i]->n * sizeof(dc_c64)});
+    s->copies->run(jobs);
+    if (cudaMemcpyAsync(in_dev, sl.in_host, (size_t)used * sizeof(dc_c64), cudaMemcpyHostToDevice,
+                        sl.stream) != cudaSuccess)
+      st = DC_ECUDA;
+  }
   if (!st)
     st = dc_internal_correct_batch_ws(sl.ctx, in_dev, out_dev, items.data(), (int)items.size(),
                                       &s->opts, sl.stream, base + 2 * io, scratch);
-  if (!st && cudaMemcpyAsync(sl.out_host, out_dev, (size_t)used * sizeof(dc_c64),
-                             cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+  if (!st && sl.direct_batch) {
+    if (n_out > 0) copy_chunks_kernel<<<n_out, 256, 0, sl.stream>>>(sl.chunks + kMaxChunks);
+    if (cudaGetLastError() != cudaSuccess) st = DC_ECUDA;
+  } else if (!st && cudaMemcpyAsync(sl.out_host, out_dev, (size_t)used * sizeof(dc_c64),
+                                    cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess) {
     st = DC_ECUDA;
+  }
   if (!st && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = DC_ECUDA;
   lk.lock();
   if (st) {
@@ -399,6 +466,16 @@ extern "C" dc_status dc_serve_start(int device, size_t hbm_budget_bytes, int slo
     return DC_ENOMEM;
   }
   s->alloc.reset(pool);
+  {
+    // direct data movement where the device reaches pageable host memory
+    // through the host's page tables
+    int pageable = 0, host_tables = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+    cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device);
+    const char* staged = getenv("DC_SERVE_STAGED");
+    s->direct = pageable && host_tables && !(staged && staged[0] == '1');
+    cudaGetLastError();
+  }
   s->slots.resize(slots);
   for (Slot& sl : s->slots) {
     sl.cap = s->cap;
@@ -409,7 +486,8 @@ extern "C" dc_status dc_serve_start(int device, size_t hbm_budget_bytes, int slo
         cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&sl.in_host, bytes) != cudaSuccess ||
-        cudaMallocHost(&sl.out_host, bytes) != cudaSuccess) {
+        cudaMallocHost(&sl.out_host, bytes) != cudaSuccess ||
+        cudaMallocHost(&sl.chunks, 2 * kMaxChunks * sizeof(CopyChunk)) != cudaSuccess) {
       cudaGetLastError();
       dc_serve_stop(s);
       return DC_ENOMEM;
@@ -520,6 +598,7 @@ extern "C" dc_status dc_serve_stop(dc_server* s) {
     if (sl.stream) cudaStreamDestroy(sl.stream);
     if (sl.in_host) cudaFreeHost(sl.in_host);
     if (sl.out_host) cudaFreeHost(sl.out_host);
+    if (sl.chunks) cudaFreeHost(sl.chunks);
   }
   if (s->pool) cudaFree(s->pool);
   for (auto& kv : s->reqs) delete kv.second;

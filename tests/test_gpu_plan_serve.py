@@ -76,8 +76,16 @@ def test_plan_bank_matches_direct_call(dcg, ctx):
     plan.close()
 
 
-def test_serve_mixed_stream_matches_alone_and_oracle(dcg, ctx):
+@pytest.mark.parametrize("staged", [False, True])
+def test_serve_mixed_stream_matches_alone_and_oracle(dcg, ctx, staged, monkeypatch):
+    # direct: copy kernels between the callers' buffers and the pool (where
+    # the device reaches pageable host memory); staged: host copies through
+    # pinned staging.  Both give every request the same bits as alone.
     import torch
+    if staged:
+        monkeypatch.setenv("DC_SERVE_STAGED", "1")
+    else:
+        monkeypatch.delenv("DC_SERVE_STAGED", raising=False)
     rng = np.random.default_rng(7)
     reqs = []
     for i in range(48):
