@@ -356,7 +356,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "p50_ms": float(np.percentile(plain_ms, 50)), "p99_ms": float(np.percentile(plain_ms, 99)),
             "pairs_timed": len(plain_ms),
             "what": "one (v_r, TEC) pair per call: doppler_resample + iono_correct launches",
-            "timing": "device fed (calls queued ahead)" if plain_fed else "host-bound (submission slower)"}
+            "timing": timing_note(plain_fed, "calls")}
 
     # ---- end to end through the C ABI with host buffers: the pulse copied
     # in from pinned memory, the corrected samples stored by the kernels
@@ -621,7 +621,7 @@ def run_batch(args) -> dict:
         "plain_path": {"value": ps / (sum(plain) / 1e3) / 1e6, "unit": UNIT,
                        "p50_ms": float(np.percentile(plain, 50)), "p99_ms": float(np.percentile(plain, 99)),
                        "pulses_timed": len(plain),
-                       "timing": "device fed (calls queued ahead)" if plain_fed else "host-bound (submission slower)"},
+                       "timing": timing_note(plain_fed, "calls")},
         "error": {"rel_l2_max": max(errs), "pulses_checked": len(errs), "tolerance": 1e-5},
         "cpu_baseline": {"value": s_or / t_or / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"the {len(errs)} checked pulses ({s_or} samples), {t_or:.1f} s"},
@@ -642,11 +642,13 @@ def device_times(torch, stream, fn, count: int, block: int = 250):
     enough for the whole block to be submitted first; the device then runs
     the block's calls back to back.  Returns (times, fed): fed is False when
     some block took longer to submit than the sleep lasted (under a profiler
-    that serialises launches, say), and those times are host-bound."""
-    out = []
-    fed = True
-    while len(out) < count:
-        nb = min(block, count - len(out))
+    that serialises launches, say), and those times are host-bound.  When at
+    least half of the blocks were fed, only the fed blocks' times are
+    returned; `fed` then is (blocks fed, blocks run)."""
+    fed_t, all_t = [], []
+    n_blocks = n_fed = 0
+    while len(all_t) < count:
+        nb = min(block, count - len(all_t))
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(nb)]
         torch.cuda.synchronize()
@@ -654,13 +656,27 @@ def device_times(torch, stream, fn, count: int, block: int = 250):
         torch.cuda._sleep(int(2.1e9 * 0.1))             # about 100 ms at the maximum SM clock
         for k, (a, b) in enumerate(ev):
             a.record(stream)
-            fn(len(out) + k)
+            fn(len(all_t) + k)
             b.record(stream)
         submit_s = time.perf_counter() - t0
         torch.cuda.synchronize()
-        fed = fed and submit_s <= 0.08                  # else the sleep did not cover them
-        out += [a.elapsed_time(b) for a, b in ev]
-    return out, fed
+        t = [a.elapsed_time(b) for a, b in ev]
+        n_blocks += 1
+        if submit_s <= 0.08:                            # else the sleep did not cover them
+            n_fed += 1
+            fed_t += t
+        all_t += t
+    if 2 * n_fed >= n_blocks:
+        return fed_t, (n_fed, n_blocks)
+    return all_t, False
+
+
+def timing_note(fed, what: str) -> str:
+    """How device_times' numbers were taken (its `fed` result)."""
+    if not fed:
+        return "host-bound (submission slower)"
+    n_fed, n_blocks = fed
+    return f"device fed ({what} queued ahead; {n_fed} of {n_blocks} blocks fed, those timed)"
 
 
 def run_plain(args) -> dict:
@@ -732,12 +748,12 @@ def run_plain(args) -> dict:
         modes[name] = {
             "value": n / (float(np.median(dev_ms)) / 1e3) / 1e6, "unit": UNIT,
             "device_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99)),
-                          "timing": "device fed (replays queued ahead)" if dev_fed else "host-bound (submission slower)"},
+                          "timing": timing_note(dev_fed, "replays")},
             "host_ms": {"p50": float(np.percentile(host_ms, 50)), "p99": float(np.percentile(host_ms, 99))},
             "graph_launches_per_pulse": launches, "replays": R,
             "kernel_us": {k: round(vv, 2) for k, vv in kern.items()},
             "plain_path": {"what": "doppler_resample + iono_correct calls, device time",
-                           "timing": "device fed (calls queued ahead)" if direct_fed else "host-bound (submission slower)",
+                           "timing": timing_note(direct_fed, "calls"),
                            "p50_ms": float(np.percentile(direct, 50)),
                            "p99_ms": float(np.percentile(direct, 99)),
                            "value": n / (float(np.median(direct)) / 1e3) / 1e6},
@@ -1082,7 +1098,7 @@ def run_paper_pulse(args) -> dict:
         p50 = float(np.percentile(ms, 50))
         out[name] = {"what": what, "device_us": {"p50": 1e3 * p50, "p99": 1e3 * float(np.percentile(ms, 99))},
                      "gsamples_per_s": L / (p50 / 1e3) / 1e9, "kernels_us": kern,
-                     "timing": "device fed (calls queued ahead)" if fed else "host-bound",
+                     "timing": timing_note(fed, "calls"),
                      "error": {"rel_l2": err, "tolerance": 1e-5},
                      "paper_h100_us": paper_us, "paper_over_ours": paper_us / (1e3 * p50),
                      "cpu_baseline": {"value": L / t_or / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -553,6 +553,7 @@ dc_status run_iono_class(dc_ctx* c, std::vector<FftItem>& it, int log2L, float2*
     if (st) return st;
     item_at += (it.size() * sizeof(FftItem) + 255) & ~(size_t)255;
     FusedArgs a{dev, (int)it.size(), log2L, c->tw, c->err, c->t4};
+    a.pdl = std::none_of(it.begin(), it.end(), [](const FftItem& f) { return f.ptab != nullptr; });
     long long outs = 0;
     for (auto& f : it) outs += f.n_out;
     Phase ph(c, PH_FUSED_FULL, s, outs);

@@ -34,6 +34,17 @@ DC_DEV float exact_i2f(int i) {
   return __int_as_float(i + 0x4B400000) - 12582912.0f;
 }
 
+// ------------------------------------------- programmatic dependent launch
+// A kernel launched with the programmatic-serialization attribute may start
+// while the kernel before it in the stream is still running; pdl_wait()
+// blocks until that kernel has completed and its memory is visible, so it
+// must come before the first access to anything the earlier kernel writes
+// or reads.  pdl_release() lets such a dependent start once every CTA of the
+// calling grid has executed it (or exited).  Both are no-ops for kernels
+// launched without the attribute or without a dependent.
+DC_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+DC_DEV void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------ double-float
 // Dekker/Knuth error-free transforms: a value is hi + lo with |lo| <= ulp(hi)/2.
 struct df { float hi, lo; };

@@ -668,10 +668,12 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
     float2 f2[4], f3[4];
     stage2_bases<-1>(f2, a.tw, j & 15);
     stage3_bases<-1>(f3, a.tw, j);
+    pdl_wait();                                 // the input's producer has finished
+    // plain loads: a non-coherent load may be scheduled ahead of the wait
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int n = j + 256 * r;
-      v[r] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+      v[r] = n < I.n_valid ? I.src[n] : make_float2(0.f, 0.f);
     }
     row4096<-1>(v, A, B, j, f2, f3);            // last reads: B after its second barrier
     const bool mult = I.ph.enabled || I.ptab;
@@ -704,6 +706,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
   } else {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");   // this CTA runs
     const float2* T = a.t4 + kT4Offset(L1);
+    pdl_wait();                                 // the input's producer has finished
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int n2 = k1 * COLS + j + 256 * p;
@@ -711,7 +714,7 @@ __global__ void __launch_bounds__(kRowThreads, LOG2L1 == 0 ? 2 : 4) full_kernel(
 #pragma unroll
       for (int n1 = 0; n1 < L1; ++n1) {
         const int n = n2 + kRowN * n1;
-        col[n1] = n < I.n_valid ? __ldg(I.src + n) : make_float2(0.f, 0.f);
+        col[n1] = n < I.n_valid ? I.src[n] : make_float2(0.f, 0.f);   // plain: after pdl_wait
       }
       dft<L1, -1>(col);
       float2 w[4];                              // W_L^(2^b n2), conjugates of the table rows
@@ -802,13 +805,18 @@ cudaError_t launch_full(const FusedArgs& a, cudaStream_t s) {
   cfg.blockDim = dim3(kRowThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  // with a.pdl, programmatic serialization: the launch may begin (items,
+  // twiddles) while the kernel before it finishes; the kernel waits for it
+  // (pdl_wait) before its first read of the input and its first store
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = L1;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = a.pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, k, a);
 }
 

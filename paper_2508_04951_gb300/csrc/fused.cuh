@@ -59,6 +59,10 @@ struct FusedArgs {
   float2* grid_dst;
   int grid_n_tec;
   int grid_n_out;
+  // FUSED_FULL: launched with programmatic serialization (set only when no
+  // item has a factor table, so that everything the kernel reads from the
+  // kernel before it -- the resampled input -- is read after pdl_wait).
+  int pdl;
 };
 
 // Four-step twiddle rows for L1 = 2, 4, 8, 16: log2(L1) rows of 4096 per L1.

@@ -71,6 +71,7 @@ DC_DEV int find_item(const RsArgs& a, int tile) {
 
 // ------------------------------------------------------------- direct
 __global__ void __launch_bounds__(kRsThreads) resample_direct_kernel(RsArgs a) {
+  pdl_release();                        // the transform that follows may start its set-up
   __shared__ int s_item;
   const int tile = blockIdx.x;
   if (threadIdx.x < 32) {
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kRsThreads) resample_direct_kernel(RsArgs a) {
 
 // ---------------------------------------------------- frequency conversion
 __global__ void __launch_bounds__(kRsThreads) freqconv_kernel(RsArgs a) {
+  pdl_release();                        // the transform that follows may start its set-up
   __shared__ int s_item;
   const int tile = blockIdx.x;
   if (threadIdx.x < 32) {
@@ -179,6 +181,7 @@ DC_DEV void tap_loop(const float2* __restrict__ w0, const float4* __restrict__ w
 
 template <int HALF, int LQ>
 __global__ void __launch_bounds__(kRsTile >> LQ) resample_tiled_kernel(RsArgs a) {
+  pdl_release();                        // the transform that follows may start its set-up
   constexpr int Q = 1 << LQ;
   constexpr int NT = kRsTile / Q;          // threads
   constexpr int W = 32 * Q;                // outputs per warp tile
@@ -520,6 +523,7 @@ DC_DEV void gemv_terms(const float2* __restrict__ x, int n_in, int np, int mn, f
 
 template <int P>
 __global__ void __launch_bounds__(256) exact_gemv_kernel(ExArgs a) {
+  pdl_release();                        // the transform that follows may start its set-up
   const ExItem& I = a.items[blockIdx.y];
   const int n = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (n >= a.n_out) return;
