@@ -107,6 +107,36 @@ DC_DEV void row4096_1buf(float2 (&v)[16], float2* b, int j, const float2* __rest
   dft16<DIR>(v);
 }
 
+// row4096_1buf with the stage bases read from shared-memory copies of the
+// table rows r = 1, 2, 4, 8 (s2: [4][16] of W256^(r k), s3: [4][256] of
+// W4096^(r j), forward values as in the table): a persistent kernel copies
+// them once, and the row's base loads then neither miss L1 nor wait on L2.
+template <int DIR>
+DC_DEV void row4096_1buf_sm(float2 (&v)[16], float2* b, int j, const float2* s2, const float2* s3) {
+  float2 w[4];
+  dft16<DIR>(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b[pad16(16 * j + r)] = v[r];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = conj_if<DIR>(s2[q * 16 + (j & 15)]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
+  apply_powers<16>(v, w);                                  // Ns = 16: W256^(r k)
+  dft16<DIR>(v);
+  const int base = (j >> 4) * 256 + (j & 15);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = conj_if<DIR>(s3[q * 256 + j]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) b[pad16(base + 16 * r)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = b[pad16(j + 256 * r)];
+  apply_powers<16>(v, w);                                  // Ns = 256: W4096^(r j)
+  dft16<DIR>(v);
+}
+
 // row4096_1buf, and once every thread has read the buffer for the last time
 // (before the last stage's twiddles and DFT) the cluster barrier is arrived
 // at with release semantics: peers may overwrite the buffer after their wait,
@@ -506,7 +536,11 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
   extern __shared__ __align__(128) float2 sm[]; // [kRowPitch] the row buffer
   __shared__ __align__(8) unsigned long long bar_in;
   __shared__ ApplyTask s_ti[2];                 // the task in hand and the next one
+  __shared__ float2 s_tw2[64], s_tw3[1024];     // the row's stage-base table rows r = 1, 2, 4, 8
   const int j = threadIdx.x;
+  if (j < 64) s_tw2[j] = __ldg(a.tw + kTwS2 + ((1 << (j >> 4)) - 1) * 16 + (j & 15));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s_tw3[q * 256 + j] = __ldg(a.tw + kTwS3 + ((1 << q) - 1) * 256 + j);
   const int P = a.chunk;
   const int n_chunks = (a.n_items + P - 1) / P;
   const int per_block = P * L1;                 // the rows (or columns) of one chunk
@@ -578,7 +612,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) apply_l2_kernel(FusedArgs a) {
         // every thread's stores (the others wait there, polling nothing)
         if (j == 0 && T.prev >= 0) wait_count(col_done + T.prev, L1, a.err);
         __syncthreads();                        // also: the row FFT overwrites sm
-        row4096_1buf<+1>(v, sm, j, a.tw);       // v[r] = Y[j + 256 r]
+        row4096_1buf_sm<+1>(v, sm, j, s_tw2, s_tw3);   // v[r] = Y[j + 256 r]
         float2* yrow = slot + (size_t)rq * kRowN;
 #pragma unroll
         for (int r = 0; r < 16; ++r) __stcg(yrow + j + 256 * r, v[r]);
