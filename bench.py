@@ -1121,13 +1121,12 @@ def run_paper_pulse(args) -> dict:
     }
 
 
-def run_sub_workloads(args, done: dict | None = None) -> dict:
+def run_sub_workloads(args) -> dict:
     """The other configurations, each in its own record with its clocks,
-    roofline or error and baselines (one GPU, after the bank); `done` holds
-    records already taken (the single pulse, measured before the bank)."""
+    roofline or error and baselines (one GPU, after the bank)."""
     import copy
     import torch
-    subs = dict(done or {})
+    subs = {}
     import gc
     # serve last: its server threads and pinned staging are torn down after
     # it, outside every other record's timed region
@@ -1137,8 +1136,6 @@ def run_sub_workloads(args, done: dict | None = None) -> dict:
             ("paper_pulse", run_paper_pulse, {}),
             ("serve", run_serve, {"serve_check_frac": min(args.serve_check_frac, 0.001)}))
     for name, fn, over in plan:
-        if name in subs:
-            continue
         gc.collect()
         torch.cuda.synchronize()
         a = copy.copy(args)
@@ -1212,19 +1209,9 @@ def main() -> None:
             args.steps = 10
         print(json.dumps(single[args.workload](args)), flush=True)
         return
-    done = {}
-    if args.workload == "all" and world == 1 and rank == 0:
-        # the single-pulse latency first, in a fresh process: after the bank's
-        # run its replays have read 14.2 instead of 12.2 us in some runs (the
-        # correction kernel's programmatic launch not overlapping the
-        # resampler; cause not found)
-        t0 = time.perf_counter()
-        done["plain"] = run_plain(args)
-        done["plain"]["bench_wall_s"] = round(time.perf_counter() - t0, 1)
-        done["plain"]["taken"] = "first in the process, before the Doppler bank"
     line = run_gpu(args, rank, world, local_rank)
     if args.workload == "all" and world == 1 and rank == 0:
-        line["workloads"] = run_sub_workloads(args, done)
+        line["workloads"] = run_sub_workloads(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

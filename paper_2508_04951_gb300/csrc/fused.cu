@@ -849,8 +849,9 @@ cudaError_t launch_full(const FusedArgs& a, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[1].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = a.pdl ? 2 : 1;
+  // L = 4096 (one CTA per transform) is no cluster launch
+  cfg.attrs = L1 > 1 ? attr : attr + 1;
+  cfg.numAttrs = (L1 > 1 ? 1 : 0) + (a.pdl ? 1 : 0);
   return cudaLaunchKernelEx(&cfg, k, a);
 }
 

@@ -503,13 +503,38 @@ __global__ void __launch_bounds__(256) exact_fp32_kernel(ExArgs a) {
 // striding the input, the weight computed once per (n, m) and applied to
 // every pulse, lanes combined by a fixed shuffle tree (deterministic).
 // One lane's share of the sum: terms m = lane, lane + 32, ... (FAST: m_n - m
-// converted by exact_i2f, valid for |m_n - m| < 2^22).
+// converted by exact_i2f, valid for |m_n - m| < 2^22).  Four terms per round:
+// their weights, then their loads, issued together so that a warp has four
+// loads in flight instead of one (the kernel is bound by the load latency);
+// the terms are still added in the order m = lane, lane + 32, ...
+template <bool FAST> DC_DEV float gemv_weight(int mn, int m, float e, float sgl) {
+  const float den = (FAST ? exact_i2f(mn - m) : (float)(mn - m)) + e;
+  return __fdividef(sgl, den);
+}
 template <int P, bool FAST>
 DC_DEV void gemv_terms(const float2* __restrict__ x, int n_in, int np, int mn, float e, float sgl,
                        int lane, float2 (&acc)[P]) {
-  for (int m = lane; m < n_in; m += 32) {
-    const float den = (FAST ? exact_i2f(mn - m) : (float)(mn - m)) + e;
-    const float w = __fdividef(sgl, den);
+  int m = lane;
+  for (; m + 96 < n_in; m += 128) {
+    float w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = gemv_weight<FAST>(mn, m + 32 * u, e, sgl);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      if (p < np) {
+        float2 xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = __ldg(x + (size_t)p * n_in + m + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc[p].x = fmaf(xv[u].x, w[u], acc[p].x);
+          acc[p].y = fmaf(xv[u].y, w[u], acc[p].y);
+        }
+      }
+    }
+  }
+  for (; m < n_in; m += 32) {
+    const float w = gemv_weight<FAST>(mn, m, e, sgl);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       if (p < np) {
