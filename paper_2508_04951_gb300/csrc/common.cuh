@@ -12,8 +12,17 @@
 namespace dc {
 
 // ---------------------------------------------------------------- complex
-DC_DEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-DC_DEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract as packed two-lane FP32 instructions (one issue
+// for both parts; each part rounds as the scalar add or subtract does).
+DC_DEV float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+DC_DEV float2 csub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 pa, pb, pr;\n mov.b64 pa, {%2, %3};\n mov.b64 pb, {%4, %5};\n"
+      " sub.rn.f32x2 pr, pa, pb;\n mov.b64 {%0, %1}, pr;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
 DC_DEV float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -110,11 +119,17 @@ template <int DIR> DC_DEV void dft2(float2& a, float2& b) {
 
 template <int DIR> DC_DEV void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
   float2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
-  float2 t2 = cadd(v1, v3), t3 = mul_i<DIR>(csub(v1, v3));
+  float2 t2 = cadd(v1, v3), d = csub(v1, v3);
   v0 = cadd(t0, t2);
   v2 = csub(t0, t2);
-  v1 = cadd(t1, t3);
-  v3 = csub(t1, t3);
+  // v1, v3 = t1 +- (-/+ i) d: the parts cross, so these four stay scalar
+  if constexpr (DIR < 0) {
+    v1 = make_float2(t1.x + d.y, t1.y - d.x);
+    v3 = make_float2(t1.x - d.y, t1.y + d.x);
+  } else {
+    v1 = make_float2(t1.x - d.y, t1.y + d.x);
+    v3 = make_float2(t1.x + d.y, t1.y - d.x);
+  }
 }
 
 // exp(DIR * 2 pi i m / 16) for a compile-time m (folded by the compiler)
