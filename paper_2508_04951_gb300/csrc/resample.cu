@@ -164,11 +164,14 @@ DC_DEV void tap_loop(const float2* __restrict__ w0, const float4* __restrict__ w
     const float4 w = wts[t];
     const float hl = fmaf(fmaf(w.z, sl, w.y), sl, w.x);
     const float dl = fmaf(w.w, sl, w.y);
+    // packed two-lane FMAs, each lane rounding as fmaf does: the weight h
+    // in both lanes, then both parts of the output at once
+    const float2 hl2 = make_float2(hl, hl), dl2 = make_float2(dl, dl);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const float h = fmaf(dl, (float)q - 0.5f * (float)(Q - 1), hl);
-      acc[q].x = fmaf(xw[q].x, h, acc[q].x);
-      acc[q].y = fmaf(xw[q].y, h, acc[q].y);
+      const float u = (float)q - 0.5f * (float)(Q - 1);
+      const float2 h2 = __ffma2_rn(dl2, make_float2(u, u), hl2);
+      acc[q] = __ffma2_rn(xw[q], h2, acc[q]);
     }
 #pragma unroll
     for (int q = 0; q + 1 < Q; ++q) xw[q] = xw[q + 1];
